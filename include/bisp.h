@@ -1,0 +1,175 @@
+/*
+ * bisp.h -- C ABI of the GB300 estimator of the redshift-space bispectrum
+ * multipoles B_l^m(k1, mu, t) of Gill & Bharadwaj, "Brisk estimator for the
+ * angular multipoles of the redshift space bispectrum" (arXiv:2405.14513).
+ *
+ * The estimator (Sec. II of the paper):
+ *   - transforms the gridded field, Delta(k) = (V/N_g^3) sum_x delta(x)
+ *     exp(-i k.x), with the line of sight along z (Eq. bs);
+ *   - splits k-space into planes n perpendicular to the line of sight and
+ *     annular rings r in each plane, ring widths 2^floor((r-1)/10) grid
+ *     units, outer radius capped at N_g/3 (Fig. 1, implementation paragraph);
+ *   - forms D(r,n,x) = sum_{u in r} Delta(u, n) exp(-i u.x) (Eq. iFT) and, for
+ *     every combination of three rings and two planes (n3 = -n1 - n2),
+ *     S = sum_x D(r1,n1) D(r2,n2) D(r3,n3) (Eq. fftbs) and the triangle count
+ *     N_tri = N_g^-2 sum_x I1 I2 I3 of the unit fields (Eqs. Ntri2, 2FT);
+ *   - maps each combination to (p, k1, mu, t) (Eqs. shape, orient) and bins
+ *     B_l^m = sqrt((2l+1)/4pi) sum Y* Bhat N_tri / sum |Y|^2 N_tri
+ *     (Eq. bs_lm2_1), Bhat = S / (V N_tri N_g^2).
+ * The library computes every step on the GPU; it has no CPU fallback.
+ *
+ * Conventions shared by all entry points:
+ *   - the input field delta[x][y][z] is real, z (the line of sight) is the
+ *     last and contiguous axis; N_g^3 values of float (precision FP32 or
+ *     MIXED) or double (precision FP64);
+ *   - the output B[batch][n_k1][n_mu][n_t][n_lm] is double; the moment axis
+ *     holds even l only, (l, m) = (0,0), (2,0), (2,1), (2,2), (4,0) ...
+ *     (l_max, l_max), so n_lm = (l_max/2 + 1)^2; empty bins hold NaN;
+ *   - k1 bins are given by edges (units of k_f = 2 pi / L); mu and t bins
+ *     are uniform on [0.5, 1], bin index floor((x - 0.5) 2 n), the top edge
+ *     closed;
+ *   - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Device pointers must be valid on the current device;
+ *   - every function returns a status code (bisp_status) and never throws
+ *     across the ABI; estimator_last_error() describes the last failure of
+ *     the calling thread.
+ */
+#ifndef BISP_H
+#define BISP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BISP_OK = 0,
+    BISP_INVALID_ARG = 1,       /* a parameter is out of range or inconsistent */
+    BISP_UNSUPPORTED_SIZE = 2,  /* N_g is not a power of two in [8, 1024]     */
+    BISP_OUT_OF_MEMORY = 3,     /* a device or host allocation failed         */
+    BISP_CUDA_ERROR = 4,        /* a CUDA call or kernel launch failed        */
+    BISP_TIMEOUT = 5,           /* a bounded device wait gave up              */
+    BISP_INTERNAL = 6           /* an internal consistency check failed       */
+} bisp_status;
+
+typedef enum {
+    BISP_PREC_FP32 = 0,   /* FP32 transforms, products and sums ("plain")          */
+    BISP_PREC_MIXED = 1,  /* FP32 transforms and products, FP64 sums and binning   */
+    BISP_PREC_FP64 = 2    /* FP64 throughout (verification)                         */
+} bisp_precision;
+
+/* Opaque plan: ring tables, triangle counts, combination tables, bin
+ * denominators and twiddles for one (N_g, L, bins, l_max, precision).  Owned
+ * by the library; created by estimator_plan, released by estimator_destroy. */
+typedef struct bisp_plan bisp_plan;
+
+typedef struct {
+    int n_g;                  /* grid points per side, power of two, 8..1024      */
+    double box_len;           /* L > 0; V = L^3, k_f = 2 pi / L                   */
+    int n_k1;                 /* number of k1 bins, >= 1                          */
+    const double *k1_edges;   /* HOST pointer, n_k1 + 1 strictly ascending edges, */
+                              /* k1_edges[n_k1] <= (N_g/3) k_f                     */
+    int n_mu, n_t;            /* uniform mu and t bins on [0.5, 1], each >= 1      */
+    int l_max;                /* even, 0..8                                        */
+    int precision;            /* bisp_precision                                    */
+    int max_batch;            /* largest batch passed to estimator_estimate, >= 1  */
+} bisp_desc;
+
+typedef struct {
+    int n_g, n_rings, n_planes;      /* rings per plane; planes 0..N_g/3 stored     */
+    int l_max, n_lm, n_k1, n_mu, n_t;
+    int n_levels;                    /* number of reduction grids in use             */
+    int64_t n_bins;                  /* n_k1 n_mu n_t                                 */
+    int64_t n_combos;                /* accepted combinations, one of each +-n pair   */
+    int64_t n_pairs;                 /* plane pairs (n1, n2) with a combination       */
+    int64_t n_items;                 /* Step-II work items (pair, grid, x chunk)      */
+    double triple_products;          /* sum over combinations of grid points summed   */
+    size_t dstore_bytes;             /* D-field store of one field                    */
+    size_t workspace_bytes;          /* estimator_workspace_bytes(plan, 1)            */
+    size_t resident_bytes;           /* device memory owned by the plan               */
+} bisp_plan_info;
+
+/* Build a plan (Sec. II: ring table, N_tri by Eq. Ntri2 on the GPU in FP64,
+ * combination table with its (k1, mu, t) bins and the field-independent
+ * denominators of Eq. bs_lm2_1).  Allocates device memory owned by the plan;
+ * work is ordered on `stream` and complete on return.  *out is set to NULL
+ * on failure. */
+int estimator_plan(bisp_plan **out, const bisp_desc *desc, void *stream);
+
+/* Plan summary.  info: host pointer. */
+int estimator_plan_info(const bisp_plan *plan, bisp_plan_info *info);
+
+/* Bytes of device workspace estimator_estimate needs for `batch` fields
+ * (0 on a bad argument).  Fields of a batch run one after the other and
+ * share the workspace, so the size does not grow with batch. */
+size_t estimator_workspace_bytes(const bisp_plan *plan, int batch);
+
+/* Estimate B_l^m for `batch` fields (1 <= batch <= max_batch).
+ *   delta:     DEVICE pointer, [batch][N_g][N_g][N_g] float or double (see
+ *              precision), read only;
+ *   workspace: DEVICE pointer to >= estimator_workspace_bytes(plan, batch)
+ *              bytes, 256-byte aligned, owned by the caller; contents are
+ *              scratch between calls;
+ *   B:         DEVICE pointer, [batch][n_k1][n_mu][n_t][n_lm] double.
+ * Asynchronous: all work is ordered on `stream`.  Calls that share a plan
+ * or a workspace must not overlap on the device. */
+int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *workspace,
+                       double *B, void *stream);
+
+/* Same estimate from and to HOST memory: copies delta in, runs, copies B out,
+ * and returns when B is complete.  The plan allocates (once, on first use)
+ * its own device workspace and staging buffers for max_batch fields. */
+int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
+                            void *stream);
+
+/* Release the plan and everything it owns (NULL is a no-op).  The caller
+ * makes sure no work that uses the plan is still running. */
+void estimator_destroy(bisp_plan *plan);
+
+/* Static description of a status code. */
+const char *estimator_status_string(int status);
+
+/* Description of the last failure on the calling thread ("" if none). */
+const char *estimator_last_error(void);
+
+/* ---------------- introspection, for tests and diagnostics ---------------- */
+
+/* Denominators sum_c |Y_lm(p_c)|^2 N_tri,c of Eq. bs_lm2_1 (counted over both
+ * members of each +-n pair).  den: HOST pointer [n_bins][n_lm]. */
+int estimator_denominator(const bisp_plan *plan, double *den);
+
+/* Accepted combinations, one of each pair (n1, n2) / (-n1, -n2), kept with
+ * n1 > 0 or (n1 == 0 and n2 >= 0), in the library's internal order.  HOST
+ * pointers with room for `cap` rows (any may be NULL):
+ *   ints[k][6] = n1, n2, n3, r1, r2, r3 (rings 0-based); ntri[k]; bin[k] =
+ *   flat (k1, mu, t) bin; grid[k] = side of the grid its sum runs on.
+ * Returns the number of combinations (even when larger than cap), < 0 on error. */
+int64_t estimator_combo_table(const bisp_plan *plan, int64_t cap, int32_t *ints, int64_t *ntri,
+                              int32_t *bin, int32_t *grid);
+
+/* After estimator_estimate on this workspace: the complex sums
+ * S = sum_x D1 D2 D3 of Eq. fftbs (full N_g^2 grid normalisation) of the last
+ * field of the batch, in estimator_combo_table order.  S: HOST pointer
+ * [n_combos][2].  Synchronises `stream`. */
+int estimator_combo_sums(const bisp_plan *plan, const void *workspace, double *S, void *stream);
+
+/* After estimator_estimate on this workspace: D(r, n, x) of Eq. iFT of the
+ * last field, sampled on the M x M grid x = (N_g/M) y, as stored for the
+ * Step-II reduction.  out: HOST pointer [M][M][2] (y_x slow, y_y fast), in
+ * double.  Returns BISP_INVALID_ARG when (M, n, r) is not stored. */
+int estimator_dfield(const bisp_plan *plan, const void *workspace, int M, int n, int r,
+                     double *out, void *stream);
+
+/* After estimator_estimate on this workspace: plane n (0 <= n <= N_g/3) of
+ * the transformed field Delta(kx, ky, n), FFT index order.  out: HOST pointer
+ * [N_g][N_g][2] double. */
+int estimator_delta_plane(const bisp_plan *plan, const void *workspace, int n, double *out,
+                          void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BISP_H */

@@ -1,0 +1,241 @@
+"""Thin Python binding of the C ABI in ``include/bisp.h`` (argument
+marshalling only; every step of the estimator runs in ``libbisp.so``).
+
+Device buffers are torch CUDA tensors (PyTorch supplies memory and
+streams); host buffers are numpy arrays.  There is no CPU fallback: if the
+CUDA library cannot be built or loaded, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PRECISIONS = {"fp32": 0, "mixed": 1, "fp64": 2}
+STATUS = {0: "BISP_OK", 1: "BISP_INVALID_ARG", 2: "BISP_UNSUPPORTED_SIZE", 3: "BISP_OUT_OF_MEMORY",
+          4: "BISP_CUDA_ERROR", 5: "BISP_TIMEOUT", 6: "BISP_INTERNAL"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BispError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+
+
+class Desc(C.Structure):
+    _fields_ = [("n_g", C.c_int), ("box_len", C.c_double), ("n_k1", C.c_int),
+                ("k1_edges", C.POINTER(C.c_double)), ("n_mu", C.c_int), ("n_t", C.c_int),
+                ("l_max", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int)]
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n_g", C.c_int), ("n_rings", C.c_int), ("n_planes", C.c_int), ("l_max", C.c_int),
+                ("n_lm", C.c_int), ("n_k1", C.c_int), ("n_mu", C.c_int), ("n_t", C.c_int),
+                ("n_levels", C.c_int), ("n_bins", C.c_int64), ("n_combos", C.c_int64),
+                ("n_pairs", C.c_int64), ("n_items", C.c_int64), ("triple_products", C.c_double),
+                ("dstore_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t),
+                ("resident_bytes", C.c_size_t)]
+
+
+def load():
+    """Build (if needed) and load libbisp.so; raises on failure."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(_build.build())
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        lib.estimator_plan.argtypes = [C.POINTER(vp), C.POINTER(Desc), vp]
+        lib.estimator_plan.restype = C.c_int
+        lib.estimator_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
+        lib.estimator_plan_info.restype = C.c_int
+        lib.estimator_workspace_bytes.argtypes = [vp, C.c_int]
+        lib.estimator_workspace_bytes.restype = C.c_size_t
+        lib.estimator_estimate.argtypes = [vp, vp, C.c_int, vp, vp, vp]
+        lib.estimator_estimate.restype = C.c_int
+        lib.estimator_estimate_host.argtypes = [vp, vp, C.c_int, vp, vp]
+        lib.estimator_estimate_host.restype = C.c_int
+        lib.estimator_destroy.argtypes = [vp]
+        lib.estimator_destroy.restype = None
+        lib.estimator_status_string.argtypes = [C.c_int]
+        lib.estimator_status_string.restype = C.c_char_p
+        lib.estimator_last_error.argtypes = []
+        lib.estimator_last_error.restype = C.c_char_p
+        lib.estimator_denominator.argtypes = [vp, dp]
+        lib.estimator_denominator.restype = C.c_int
+        lib.estimator_combo_table.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
+        lib.estimator_combo_table.restype = C.c_int64
+        lib.estimator_combo_sums.argtypes = [vp, vp, dp, vp]
+        lib.estimator_combo_sums.restype = C.c_int
+        lib.estimator_dfield.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, dp, vp]
+        lib.estimator_dfield.restype = C.c_int
+        lib.estimator_delta_plane.argtypes = [vp, vp, C.c_int, dp, vp]
+        lib.estimator_delta_plane.restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise BispError(status, where, load().estimator_last_error().decode())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def even_moments(l_max: int):
+    """(l, m) of the moment axis of B: even l, 0 <= m <= l."""
+    return [(l, m) for l in range(0, l_max + 1, 2) for m in range(l + 1)]
+
+
+class Plan:
+    """An estimator plan (``estimator_plan``) and its calls."""
+
+    def __init__(self, n_g: int, box_len: float, k1_edges, n_mu: int, n_t: int, l_max: int,
+                 precision: str = "mixed", max_batch: int = 1, stream=None):
+        lib = load()
+        self._edges = np.ascontiguousarray(k1_edges, dtype=np.float64)
+        self.n_g, self.box_len, self.n_mu, self.n_t, self.l_max = n_g, box_len, n_mu, n_t, l_max
+        self.n_k1 = len(self._edges) - 1
+        self.precision = precision
+        self.max_batch = max_batch
+        d = Desc(n_g, box_len, self.n_k1, _dp(self._edges), n_mu, n_t, l_max,
+                 PRECISIONS[precision], max_batch)
+        h = C.c_void_p()
+        st = lib.estimator_plan(C.byref(h), C.byref(d), _stream_handle(stream) if stream is not None
+                                else C.c_void_p(0))
+        _check(st, "estimator_plan")
+        self._h = h
+        inf = PlanInfo()
+        _check(lib.estimator_plan_info(h, C.byref(inf)), "estimator_plan_info")
+        self.info = {k: getattr(inf, k) for k, _ in PlanInfo._fields_}
+        self.n_lm = inf.n_lm
+        self.n_bins = inf.n_bins
+        self.n_combos = inf.n_combos
+        self.field_dtype = np.float64 if precision == "fp64" else np.float32
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().estimator_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def out_shape(self, batch: int = 1):
+        return (batch, self.n_k1, self.n_mu, self.n_t, self.n_lm)
+
+    def workspace_bytes(self, batch: int = 1) -> int:
+        return int(load().estimator_workspace_bytes(self._h, batch))
+
+    def workspace(self, batch: int = 1, device="cuda"):
+        import torch
+        return torch.empty(max(self.workspace_bytes(batch), 256), dtype=torch.uint8, device=device)
+
+    def estimate(self, delta, workspace, out=None, stream=None):
+        """delta: CUDA tensor [batch][N][N][N] (float32, or float64 for fp64);
+        returns (or fills) a CUDA float64 tensor [batch][n_k1][n_mu][n_t][n_lm]."""
+        import torch
+        if delta.dim() == 3:
+            delta = delta.unsqueeze(0)
+        batch = delta.shape[0]
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if delta.dtype != want or not delta.is_cuda or not delta.is_contiguous():
+            raise ValueError(f"delta must be a contiguous CUDA {want} tensor")
+        if tuple(delta.shape[1:]) != (self.n_g,) * 3:
+            raise ValueError("delta has the wrong grid size")
+        if out is None:
+            out = torch.empty(self.out_shape(batch), dtype=torch.float64, device=delta.device)
+        st = load().estimator_estimate(self._h, C.c_void_p(delta.data_ptr()), batch,
+                                       C.c_void_p(workspace.data_ptr()), C.c_void_p(out.data_ptr()),
+                                       _stream_handle(stream))
+        _check(st, "estimator_estimate")
+        return out
+
+    def estimate_host(self, delta: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Host-memory variant: numpy in, numpy out (copies inside the call)."""
+        d = np.ascontiguousarray(delta, dtype=self.field_dtype)
+        if d.ndim == 3:
+            d = d[None]
+        if out is None:
+            out = np.empty(self.out_shape(d.shape[0]), dtype=np.float64)
+        st = load().estimator_estimate_host(self._h, C.c_void_p(d.ctypes.data), d.shape[0],
+                                            C.c_void_p(out.ctypes.data),
+                                            _stream_handle(stream) if stream is not None else C.c_void_p(0))
+        _check(st, "estimator_estimate_host")
+        return out
+
+    # ------------------------------------------------------------------
+    def denominator(self) -> np.ndarray:
+        den = np.zeros((self.n_bins, self.n_lm))
+        _check(load().estimator_denominator(self._h, _dp(den)), "estimator_denominator")
+        return den.reshape(self.n_k1, self.n_mu, self.n_t, self.n_lm)
+
+    def combo_table(self):
+        n = self.n_combos
+        ints = np.zeros((max(n, 1), 6), dtype=np.int32)
+        ntri = np.zeros(max(n, 1), dtype=np.int64)
+        binv = np.zeros(max(n, 1), dtype=np.int32)
+        grid = np.zeros(max(n, 1), dtype=np.int32)
+        got = load().estimator_combo_table(self._h, n, C.c_void_p(ints.ctypes.data),
+                                           C.c_void_p(ntri.ctypes.data), C.c_void_p(binv.ctypes.data),
+                                           C.c_void_p(grid.ctypes.data))
+        if got != n:
+            raise BispError(6, "estimator_combo_table", "count mismatch")
+        return {"ints": ints[:n], "ntri": ntri[:n], "bin": binv[:n], "grid": grid[:n]}
+
+    def combo_sums(self, workspace, stream=None) -> np.ndarray:
+        S = np.zeros(max(self.n_combos, 1))
+        _check(load().estimator_combo_sums(self._h, C.c_void_p(workspace.data_ptr()), _dp(S),
+                                           _stream_handle(stream)), "estimator_combo_sums")
+        return S[: self.n_combos]
+
+    def dfield(self, workspace, M: int, n: int, r: int, stream=None) -> np.ndarray:
+        out = np.zeros((M, M, 2))
+        _check(load().estimator_dfield(self._h, C.c_void_p(workspace.data_ptr()), M, n, r, _dp(out),
+                                       _stream_handle(stream)), "estimator_dfield")
+        return out[..., 0] + 1j * out[..., 1]
+
+    def delta_plane(self, workspace, n: int, stream=None) -> np.ndarray:
+        out = np.zeros((self.n_g, self.n_g, 2))
+        _check(load().estimator_delta_plane(self._h, C.c_void_p(workspace.data_ptr()), n, _dp(out),
+                                            _stream_handle(stream)), "estimator_delta_plane")
+        return out[..., 0] + 1j * out[..., 1]
+
+
+def status_string(status: int) -> str:
+    return load().estimator_status_string(status).decode()
+
+
+def try_plan(n_g, box_len, k1_edges, n_mu, n_t, l_max, precision="mixed", max_batch=1):
+    """Call estimator_plan and return (status, last_error); destroys any plan.
+    Used to check argument validation."""
+    lib = load()
+    e = np.ascontiguousarray(k1_edges, dtype=np.float64)
+    d = Desc(n_g, box_len, len(e) - 1, _dp(e), n_mu, n_t, l_max, PRECISIONS.get(precision, precision),
+             max_batch)
+    h = C.c_void_p()
+    st = lib.estimator_plan(C.byref(h), C.byref(d), C.c_void_p(0))
+    if h.value:
+        lib.estimator_destroy(h)
+    return st, lib.estimator_last_error().decode()

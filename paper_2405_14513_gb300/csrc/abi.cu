@@ -1,0 +1,598 @@
+// abi.cu -- the C ABI of include/bisp.h: plan construction, workspace layout
+// and the stream-ordered estimate (forward transform, Step I, Step II,
+// binning) of Gill & Bharadwaj, arXiv:2405.14513, Sec. II.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "bisp.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+using namespace bisp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(x)                                                                                     \
+    do {                                                                                          \
+        cudaError_t e_ = (x);                                                                     \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(e_ == cudaErrorMemoryAllocation ? BISP_OUT_OF_MEMORY : BISP_CUDA_ERROR,   \
+                        std::string(#x) + ": " + cudaGetErrorString(e_));                         \
+    } while (0)
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int64_t kXChunk = 65536;        // grid points of one Step-II item
+constexpr size_t kStep2SmemBudget = 200 * 1024;
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+int ilog2i(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+}  // namespace
+
+struct bisp_plan {
+    HostPlan hp;
+    int precision = BISP_PREC_MIXED;
+    size_t celem = 8;                    // bytes of one complex field value
+    std::vector<void *> owned;           // device allocations of the plan
+    Group *d_groups = nullptr;
+    Segment *d_segs = nullptr;
+    Item *d_items = nullptr;
+    int64_t *d_doff = nullptr;
+    Record *d_rec = nullptr;
+    int64_t *d_bin_start = nullptr;
+    double *d_den = nullptr;
+    std::vector<double> h_den;
+    float2 *d_tw_f = nullptr;
+    double2 *d_tw_d = nullptr;
+    int lg_tw = 0;
+    RingArg ring_arg{};
+    std::vector<Job *> d_jobs;           // per level in use
+    std::vector<int64_t *> d_job_off;    // per level: output offsets of the jobs
+    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, ws_bytes = 0;
+    int tx = 0;
+    size_t step2_smem = 0;
+    size_t resident = 0;
+    // buffers of estimator_estimate_host
+    void *own_ws = nullptr, *own_in = nullptr;
+    double *own_out = nullptr;
+};
+
+namespace {
+
+template <typename T>
+int dev_alloc(bisp_plan *p, T **out, size_t count)
+{
+    void *q = nullptr;
+    size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BISP_OUT_OF_MEMORY, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " +
+                                            cudaGetErrorString(e));
+    }
+    p->owned.push_back(q);
+    p->resident += bytes;
+    *out = static_cast<T *>(q);
+    return BISP_OK;
+}
+
+template <typename T>
+int upload(bisp_plan *p, T **out, const std::vector<T> &v, cudaStream_t s)
+{
+    int st = dev_alloc(p, out, v.size());
+    if (st) return st;
+    if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return BISP_OK;
+}
+
+void free_plan(bisp_plan *p)
+{
+    if (!p) return;
+    for (void *q : p->owned) cudaFree(q);
+    if (p->own_ws) cudaFree(p->own_ws);
+    if (p->own_in) cudaFree(p->own_in);
+    if (p->own_out) cudaFree(p->own_out);
+    delete p;
+}
+
+int check_desc(const bisp_desc *d)
+{
+    if (!d) return fail(BISP_INVALID_ARG, "desc is NULL");
+    if (d->n_g < 8 || d->n_g > 1024 || (d->n_g & (d->n_g - 1)))
+        return fail(BISP_UNSUPPORTED_SIZE, "n_g must be a power of two in [8, 1024]");
+    if (!(d->box_len > 0) || !std::isfinite(d->box_len)) return fail(BISP_INVALID_ARG, "box_len must be > 0");
+    if (d->n_k1 < 1 || !d->k1_edges) return fail(BISP_INVALID_ARG, "need n_k1 >= 1 and k1_edges");
+    for (int b = 0; b < d->n_k1; ++b)
+        if (!(d->k1_edges[b] < d->k1_edges[b + 1])) return fail(BISP_INVALID_ARG, "k1_edges must ascend strictly");
+    if (!(d->k1_edges[0] >= 0)) return fail(BISP_INVALID_ARG, "k1_edges must be >= 0");
+    const double kf = kTwoPi / d->box_len;
+    if (d->k1_edges[d->n_k1] > (d->n_g / 3.0) * kf * (1.0 + 1e-12))
+        return fail(BISP_INVALID_ARG, "k1_edges beyond (N_g/3) k_f alias");
+    if (d->n_mu < 1 || d->n_t < 1 || d->n_mu > 4096 || d->n_t > 4096)
+        return fail(BISP_INVALID_ARG, "n_mu and n_t must be in [1, 4096]");
+    if (d->l_max < 0 || d->l_max > 8 || (d->l_max & 1)) return fail(BISP_INVALID_ARG, "l_max must be even, 0..8");
+    if (d->precision < BISP_PREC_FP32 || d->precision > BISP_PREC_FP64)
+        return fail(BISP_INVALID_ARG, "unknown precision");
+    if (d->max_batch < 1) return fail(BISP_INVALID_ARG, "max_batch must be >= 1");
+    return BISP_OK;
+}
+
+// N_tri of every ring triple by Eq. Ntri2 on the GPU in FP64: unit fields
+// I(r) on each reduction grid, then M^-2 sum_y I1 I2 I3, rounded.
+int compute_ntri(bisp_plan *p, cudaStream_t s)
+{
+    HostPlan &P = p->hp;
+    const Rings &R = P.rings;
+    const int nr = R.nr;
+    std::vector<int32_t> tri;
+    std::vector<uint8_t> need(size_t(kMaxLevels) * kMaxRings, 0);
+    for (int a = 0; a < nr; ++a)
+        for (int b = a; b < nr; ++b)
+            for (int c = b; c < nr; ++c) {
+                int lg = triple_log2m(R, a, b, c);
+                tri.insert(tri.end(), {a, b, c, lg});
+                need[lg * kMaxRings + a] = need[lg * kMaxRings + b] = need[lg * kMaxRings + c] = 1;
+            }
+    std::vector<int64_t> ioff(size_t(kMaxLevels) * kMaxRings, -1);
+    int64_t cur = 0, gtmax = 0;
+    std::vector<std::vector<Job>> jobs(kMaxLevels);
+    for (int lg = kMinLog2M; lg < kMaxLevels; ++lg)
+        for (int r = 0; r < nr; ++r)
+            if (need[lg * kMaxRings + r]) {
+                ioff[lg * kMaxRings + r] = cur;
+                jobs[lg].push_back(Job{0, r, cur});
+                cur += int64_t(1) << (2 * lg);
+            }
+    for (int lg = kMinLog2M; lg < kMaxLevels; ++lg)
+        gtmax = std::max<int64_t>(gtmax, int64_t(jobs[lg].size()) << (2 * lg));
+
+    std::vector<void *> tmp;
+    auto talloc = [&](size_t bytes) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        tmp.push_back(q);
+        return q;
+    };
+    auto cleanup = [&]() { for (void *q : tmp) cudaFree(q); };
+    double2 *I = (double2 *)talloc(size_t(cur) * sizeof(double2));
+    double2 *gt = (double2 *)talloc(size_t(gtmax) * sizeof(double2));
+    int64_t *d_ioff = (int64_t *)talloc(ioff.size() * sizeof(int64_t));
+    int32_t *d_tri = (int32_t *)talloc(tri.size() * sizeof(int32_t));
+    double *d_raw = (double *)talloc(tri.size() / 4 * sizeof(double));
+    Job *d_jobs = (Job *)talloc(size_t(nr) * sizeof(Job));
+    int64_t *d_joff = (int64_t *)talloc(size_t(nr) * sizeof(int64_t));
+    if (!I || !gt || !d_ioff || !d_tri || !d_raw || !d_jobs || !d_joff) {
+        cleanup();
+        return fail(BISP_OUT_OF_MEMORY, "device memory for the triangle counts");
+    }
+    auto run = [&]() -> int {
+        CK(cudaMemcpyAsync(d_ioff, ioff.data(), ioff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(d_tri, tri.data(), tri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        for (int lg = kMinLog2M; lg < kMaxLevels; ++lg) {
+            if (jobs[lg].empty()) continue;
+            const int M = 1 << lg;
+            std::vector<int64_t> joff;
+            for (auto &j : jobs[lg]) joff.push_back(j.out_off);
+            CK(cudaMemcpyAsync(d_jobs, jobs[lg].data(), jobs[lg].size() * sizeof(Job), cudaMemcpyHostToDevice, s));
+            CK(cudaMemcpyAsync(d_joff, joff.data(), joff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+            CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lg].size()), M, true, gt,
+                                          p->d_tw_d, p->lg_tw, s));
+            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lg].size()), d_joff, 1.0, false, p->d_tw_d,
+                                         p->lg_tw, s));
+            CK(cudaStreamSynchronize(s));   // the job tables are reused by the next grid
+        }
+        CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), d_raw, s));
+        std::vector<double> raw(tri.size() / 4);
+        CK(cudaMemcpyAsync(raw.data(), d_raw, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        P.ntri.assign(size_t(nr) * nr * nr, 0);
+        for (size_t t = 0; t < raw.size(); ++t) {
+            const double v = raw[t], rv = std::nearbyint(v);
+            if (!(std::fabs(v - rv) < 1e-3) || rv < 0)
+                return fail(BISP_INTERNAL, "triangle count not an integer: " + std::to_string(v));
+            const int a = tri[4 * t], b = tri[4 * t + 1], c = tri[4 * t + 2];
+            const int64_t n = int64_t(rv);
+            const int perm[6][3] = {{a, b, c}, {a, c, b}, {b, a, c}, {b, c, a}, {c, a, b}, {c, b, a}};
+            for (auto &q : perm) P.ntri[(size_t(q[0]) * nr + q[1]) * nr + q[2]] = n;
+        }
+        return BISP_OK;
+    };
+    int st = run();
+    cudaStreamSynchronize(s);
+    cleanup();
+    return st;
+}
+
+int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
+{
+    HostPlan &P = p->hp;
+    P.desc = *desc;
+    P.k1_edges.assign(desc->k1_edges, desc->k1_edges + desc->n_k1 + 1);
+    P.desc.k1_edges = P.k1_edges.data();
+    P.kf = kTwoPi / desc->box_len;
+    P.volume = desc->box_len * desc->box_len * desc->box_len;
+    P.n_lm = (desc->l_max / 2 + 1) * (desc->l_max / 2 + 1);
+    P.n_bins = int64_t(desc->n_k1) * desc->n_mu * desc->n_t;
+    p->precision = desc->precision;
+    p->celem = desc->precision == BISP_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    if (!build_rings(desc->n_g, P.rings)) return fail(BISP_UNSUPPORTED_SIZE, "ring table");
+    const Rings &R = P.rings;
+    p->ring_arg.nr = R.nr;
+    for (int r = 0; r <= R.nr; ++r) p->ring_arg.e3sq[r] = R.e3[r] * R.e3[r];
+    for (int r = 0; r < R.nr; ++r) p->ring_arg.maxc[r] = R.maxc[r];
+
+    // twiddles exp(-2 pi i k / N_g), k < N_g / 2, in double
+    p->lg_tw = ilog2i(desc->n_g);
+    {
+        const int h = desc->n_g / 2;
+        std::vector<double2> twd(h);
+        std::vector<float2> twf(h);
+        for (int k = 0; k < h; ++k) {
+            const double a = -kTwoPi * double(k) / double(desc->n_g);
+            twd[k] = make_double2(std::cos(a), std::sin(a));
+            twf[k] = make_float2(float(twd[k].x), float(twd[k].y));
+        }
+        int st = upload(p, &p->d_tw_d, twd, s);
+        if (!st) st = upload(p, &p->d_tw_f, twf, s);
+        if (st) return st;
+    }
+    // Y_lm normalisations
+    {
+        double nlm[9][9] = {}, pref[9] = {};
+        for (int l = 0; l <= 8; ++l) {
+            pref[l] = std::sqrt((2.0 * l + 1.0) / (2.0 * kTwoPi));
+            for (int m = 0; m <= l; ++m) {
+                double r = 1.0;
+                for (int k = l - m + 1; k <= l + m; ++k) r /= double(k);
+                nlm[l][m] = std::sqrt((2.0 * l + 1.0) / (2.0 * kTwoPi) * r);
+            }
+        }
+        CK(set_ylm_constants(nlm, pref, s));
+    }
+    int st = compute_ntri(p, s);
+    if (st) return st;
+    std::string err = enumerate(P, kXChunk);
+    if (!err.empty()) return fail(BISP_INTERNAL, err);
+    sort_records(P);
+
+    st = upload(p, &p->d_groups, P.groups, s);
+    if (!st) st = upload(p, &p->d_segs, P.segs, s);
+    if (!st) st = upload(p, &p->d_items, P.items, s);
+    if (!st) st = upload(p, &p->d_doff, P.doff, s);
+    if (!st) st = upload(p, &p->d_rec, P.records, s);
+    if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
+    if (!st) st = dev_alloc(p, &p->d_den, size_t(P.n_bins) * P.n_lm);
+    if (st) return st;
+    // plan-time denominators of Eq. bs_lm2_1 (FP64)
+    {
+        double *d_nt = nullptr;
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(P.rec_ntri.size() * sizeof(double), 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BISP_OUT_OF_MEMORY, "device memory for the denominators");
+        }
+        d_nt = static_cast<double *>(q);
+        cudaError_t e = cudaMemcpyAsync(d_nt, P.rec_ntri.data(), P.rec_ntri.size() * sizeof(double),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = launch_epilogue<double>(1, p->d_rec, p->d_bin_start, P.n_bins, d_nt, desc->l_max, nullptr, 1.0,
+                                        p->d_den, s);
+        p->h_den.resize(size_t(P.n_bins) * P.n_lm);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->h_den.data(), p->d_den, p->h_den.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_nt);
+        if (e != cudaSuccess) return fail(BISP_CUDA_ERROR, std::string("denominators: ") + cudaGetErrorString(e));
+        std::vector<double>().swap(P.rec_ntri);
+    }
+    // Step-I jobs per grid
+    for (const Level &L : P.levels) {
+        std::vector<Job> jobs;
+        std::vector<int64_t> off;
+        for (int n = 0; n <= R.nz; ++n)
+            for (int r = 0; r < R.nr; ++r) {
+                int64_t o = P.doff[(size_t(L.log2m) * (R.nz + 1) + n) * kMaxRings + r];
+                if (o >= 0) {
+                    jobs.push_back(Job{n, r, o});
+                    off.push_back(o);
+                }
+            }
+        Job *dj = nullptr;
+        int64_t *dof = nullptr;
+        st = upload(p, &dj, jobs, s);
+        if (!st) st = upload(p, &dof, off, s);
+        if (st) return st;
+        p->d_jobs.push_back(dj);
+        p->d_job_off.push_back(dof);
+    }
+    // workspace layout
+    const int64_t planes = int64_t(R.nz + 1) * desc->n_g * desc->n_g;
+    size_t o = 0;
+    p->off_a = o; o = align256(o + size_t(planes) * p->celem);
+    p->off_b = o; o = align256(o + size_t(planes) * p->celem);
+    p->off_gt = o; o = align256(o + size_t(P.gt_elems) * p->celem);
+    p->off_dstore = o; o = align256(o + size_t(P.dstore_elems) * p->celem);
+    p->off_part = o; o = align256(o + size_t(P.n_partials) * sizeof(double));
+    p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
+    p->ws_bytes = o;
+    // Step-II tile: the rings of three planes for TX points, plus block sums
+    int ncmax = 0, nsmax = 1;
+    for (const Group &G : P.groups) {
+        ncmax = std::max(ncmax, G.ncombo);
+        nsmax = std::max(nsmax, (G.rhi[0] - G.rlo[0] + 1) + (G.rhi[1] - G.rlo[1] + 1) + (G.rhi[2] - G.rlo[2] + 1));
+    }
+    const size_t ssum = desc->precision == BISP_PREC_FP32 ? sizeof(float) : sizeof(double);
+    const size_t fixed = ((size_t(ncmax) * ssum + 15) & ~size_t(15)) + size_t(nsmax) * 12 + 32;
+    if (fixed + size_t(nsmax) * 33 * p->celem > kStep2SmemBudget)
+        return fail(BISP_INTERNAL, "Step-II group too large for shared memory");
+    int tx = int((kStep2SmemBudget - fixed) / (size_t(nsmax) * p->celem)) - 1;
+    tx = std::min(512, tx - tx % 32);
+    p->tx = tx;
+    p->step2_smem = fixed + size_t(nsmax) * (tx + 1) * p->celem;
+    CK(cudaStreamSynchronize(s));
+    return BISP_OK;
+}
+
+template <typename R, typename A, typename S, typename W>
+int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, double *B, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    const HostPlan &P = p->hp;
+    const Rings &Rg = P.rings;
+    const int ng = P.desc.n_g;
+    const C *tw = reinterpret_cast<const C *>(sizeof(R) == 8 ? (const void *)p->d_tw_d : (const void *)p->d_tw_f);
+    C *A_ = reinterpret_cast<C *>(ws + p->off_a);
+    C *B_ = reinterpret_cast<C *>(ws + p->off_b);
+    C *gt = reinterpret_cast<C *>(ws + p->off_gt);
+    C *dstore = reinterpret_cast<C *>(ws + p->off_dstore);
+    double *part = reinterpret_cast<double *>(ws + p->off_part);
+    double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
+    const int64_t ng2 = int64_t(ng) * ng;
+    const R scale = R(P.volume / (double(ng2) * ng));
+    StepIIArgs a2{p->d_groups, p->d_segs, p->d_items, p->d_doff, Rg.nz + 1, kXChunk, p->tx, part};
+    for (int b = 0; b < batch; ++b) {
+        const R *d = delta + int64_t(b) * ng2 * ng;
+        // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
+        CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, p->lg_tw, s));
+        CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, p->lg_tw, s));
+        CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, p->lg_tw, s));
+        // Step I: D(r, n) on each reduction grid (Eq. iFT)
+        for (size_t l = 0; l < P.levels.size(); ++l) {
+            const Level &L = P.levels[l];
+            const int M = 1 << L.log2m;
+            CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, p->lg_tw, s));
+            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, p->lg_tw, s));
+        }
+        // Step II: triple sums (Eq. fftbs)
+        CK((launch_step2<R, A, S>(a2, dstore, int64_t(P.items.size()), p->step2_smem, s)));
+        using RA = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
+        CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, s));
+        // binning and the ratio of Eq. bs_lm2_1
+        CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
+                              1.0 / (P.volume * double(ng2)), B + int64_t(b) * P.n_bins * P.n_lm, s));
+    }
+    return BISP_OK;
+}
+
+int dispatch_estimate(bisp_plan *p, const void *delta, int batch, void *ws, double *B, cudaStream_t s)
+{
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    switch (p->precision) {
+    case BISP_PREC_FP32:
+        return run_estimate<float, float, float, float>(p, static_cast<const float *>(delta), batch, w, B, s);
+    case BISP_PREC_MIXED:
+        return run_estimate<float, float, double, double>(p, static_cast<const float *>(delta), batch, w, B, s);
+    default:
+        return run_estimate<double, double, double, double>(p, static_cast<const double *>(delta), batch, w, B, s);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int estimator_plan(bisp_plan **out, const bisp_desc *desc, void *stream)
+{
+    g_err.clear();
+    if (!out) return fail(BISP_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int st = check_desc(desc);
+    if (st) return st;
+    bisp_plan *p = nullptr;
+    try {
+        p = new bisp_plan();
+        st = build_plan(p, desc, static_cast<cudaStream_t>(stream));
+    } catch (const std::bad_alloc &) {
+        st = fail(BISP_OUT_OF_MEMORY, "host allocation failed while planning");
+    } catch (const std::exception &e) {
+        st = fail(BISP_INTERNAL, e.what());
+    }
+    if (st) {
+        free_plan(p);
+        return st;
+    }
+    *out = p;
+    return BISP_OK;
+}
+
+int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
+{
+    if (!p || !info) return fail(BISP_INVALID_ARG, "NULL argument");
+    const HostPlan &P = p->hp;
+    info->n_g = P.desc.n_g;
+    info->n_rings = P.rings.nr;
+    info->n_planes = P.rings.nz + 1;
+    info->l_max = P.desc.l_max;
+    info->n_lm = P.n_lm;
+    info->n_k1 = P.desc.n_k1;
+    info->n_mu = P.desc.n_mu;
+    info->n_t = P.desc.n_t;
+    info->n_levels = int(P.levels.size());
+    info->n_bins = P.n_bins;
+    info->n_combos = P.n_combos;
+    info->n_pairs = P.n_pairs;
+    info->n_items = int64_t(P.items.size());
+    info->triple_products = P.triple_products;
+    info->dstore_bytes = size_t(P.dstore_elems) * p->celem;
+    info->workspace_bytes = p->ws_bytes;
+    info->resident_bytes = p->resident;
+    return BISP_OK;
+}
+
+size_t estimator_workspace_bytes(const bisp_plan *p, int batch)
+{
+    if (!p || batch < 1 || batch > p->hp.desc.max_batch) return 0;
+    return p->ws_bytes;
+}
+
+int estimator_estimate(bisp_plan *p, const void *delta, int batch, void *workspace, double *B, void *stream)
+{
+    g_err.clear();
+    if (!p || !delta || !workspace || !B) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(BISP_INVALID_ARG, "workspace not 256-byte aligned");
+    return dispatch_estimate(p, delta, batch, workspace, B, static_cast<cudaStream_t>(stream));
+}
+
+int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, double *B_host, void *stream)
+{
+    g_err.clear();
+    if (!p || !delta_host || !B_host) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const HostPlan &P = p->hp;
+    const size_t field = size_t(P.desc.n_g) * P.desc.n_g * P.desc.n_g *
+                         (p->precision == BISP_PREC_FP64 ? sizeof(double) : sizeof(float));
+    const size_t outb = size_t(P.n_bins) * P.n_lm * sizeof(double);
+    if (!p->own_ws) {
+        CK(cudaMalloc(&p->own_ws, std::max<size_t>(p->ws_bytes, 256)));
+        CK(cudaMalloc(&p->own_in, field * P.desc.max_batch));
+        CK(cudaMalloc((void **)&p->own_out, outb * P.desc.max_batch));
+    }
+    CK(cudaMemcpyAsync(p->own_in, delta_host, field * batch, cudaMemcpyHostToDevice, s));
+    int st = dispatch_estimate(p, p->own_in, batch, p->own_ws, p->own_out, s);
+    if (st) return st;
+    CK(cudaMemcpyAsync(B_host, p->own_out, outb * batch, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return BISP_OK;
+}
+
+void estimator_destroy(bisp_plan *p) { free_plan(p); }
+
+const char *estimator_status_string(int status)
+{
+    switch (status) {
+    case BISP_OK: return "ok";
+    case BISP_INVALID_ARG: return "invalid argument";
+    case BISP_UNSUPPORTED_SIZE: return "unsupported grid size";
+    case BISP_OUT_OF_MEMORY: return "out of memory";
+    case BISP_CUDA_ERROR: return "CUDA error";
+    case BISP_TIMEOUT: return "device wait timed out";
+    case BISP_INTERNAL: return "internal error";
+    default: return "unknown status";
+    }
+}
+
+const char *estimator_last_error(void) { return g_err.c_str(); }
+
+int estimator_denominator(const bisp_plan *p, double *den)
+{
+    if (!p || !den) return fail(BISP_INVALID_ARG, "NULL argument");
+    std::memcpy(den, p->h_den.data(), p->h_den.size() * sizeof(double));
+    return BISP_OK;
+}
+
+int64_t estimator_combo_table(const bisp_plan *p, int64_t cap, int32_t *ints, int64_t *ntri, int32_t *bin,
+                              int32_t *grid)
+{
+    if (!p) return -1;
+    const HostPlan &P = p->hp;
+    const int nr = P.rings.nr;
+    for (const Group &G : P.groups)
+        for (int s = 0; s < G.nseg; ++s) {
+            const Segment &q = P.segs[G.seg0 + s];
+            for (int j = 0; j < q.n; ++j) {
+                const int64_t k = G.c0 + q.coff + j;
+                if (k >= cap) continue;
+                const int r3 = q.r3a + j;
+                if (ints) {
+                    int32_t *o = ints + 6 * k;
+                    o[0] = G.n1; o[1] = G.n2; o[2] = G.n3;
+                    o[3] = q.r1; o[4] = q.r2; o[5] = r3;
+                }
+                if (ntri) ntri[k] = P.ntri[(size_t(q.r1) * nr + q.r2) * nr + r3];
+                if (bin) bin[k] = P.combo_bin[k];
+                if (grid) grid[k] = 1 << G.log2m;
+            }
+        }
+    return P.n_combos;
+}
+
+int estimator_combo_sums(const bisp_plan *p, const void *workspace, double *S, void *stream)
+{
+    if (!p || !workspace || !S) return fail(BISP_INVALID_ARG, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CK(cudaMemcpyAsync(S, static_cast<const unsigned char *>(workspace) + p->off_S,
+                       size_t(p->hp.n_combos) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return BISP_OK;
+}
+
+static int copy_complex_out(const bisp_plan *p, const unsigned char *src, int64_t n, double *out, cudaStream_t s)
+{
+    if (p->celem == sizeof(double2)) {
+        CK(cudaMemcpyAsync(out, src, size_t(n) * 16, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    } else {
+        std::vector<float> tmp(size_t(n) * 2);
+        CK(cudaMemcpyAsync(tmp.data(), src, size_t(n) * 8, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < tmp.size(); ++i) out[i] = tmp[i];
+    }
+    return BISP_OK;
+}
+
+int estimator_dfield(const bisp_plan *p, const void *workspace, int M, int n, int r, double *out, void *stream)
+{
+    if (!p || !workspace || !out) return fail(BISP_INVALID_ARG, "NULL argument");
+    const HostPlan &P = p->hp;
+    if (M < 8 || (M & (M - 1)) || M > P.desc.n_g || n < 0 || n > P.rings.nz || r < 0 || r >= P.rings.nr)
+        return fail(BISP_INVALID_ARG, "no such field");
+    const int lg = ilog2i(M);
+    const int64_t o = P.doff[(size_t(lg) * (P.rings.nz + 1) + n) * kMaxRings + r];
+    if (o < 0) return fail(BISP_INVALID_ARG, "field not stored on this grid");
+    const unsigned char *src = static_cast<const unsigned char *>(workspace) + p->off_dstore + size_t(o) * p->celem;
+    return copy_complex_out(p, src, int64_t(M) * M, out, static_cast<cudaStream_t>(stream));
+}
+
+int estimator_delta_plane(const bisp_plan *p, const void *workspace, int n, double *out, void *stream)
+{
+    if (!p || !workspace || !out) return fail(BISP_INVALID_ARG, "NULL argument");
+    const HostPlan &P = p->hp;
+    if (n < 0 || n > P.rings.nz) return fail(BISP_INVALID_ARG, "plane out of range");
+    const int64_t ng2 = int64_t(P.desc.n_g) * P.desc.n_g;
+    const unsigned char *src = static_cast<const unsigned char *>(workspace) + p->off_a + size_t(n) * ng2 * p->celem;
+    return copy_complex_out(p, src, ng2, out, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

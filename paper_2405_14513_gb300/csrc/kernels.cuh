@@ -1,0 +1,94 @@
+// kernels.cuh -- device kernels of the bispectrum-multipole estimator and
+// their launch helpers.  Internal to libbisp.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace bisp {
+
+template <typename R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+
+// Ring table as a kernel argument (membership by the integer test of
+// build_rings).
+struct RingArg {
+    int nr;
+    int64_t e3sq[kMaxRings + 1];   // (3 e_r)^2
+    int maxc[kMaxRings];
+};
+
+// Step-I job: one (plane, ring) field on one reduction grid.
+struct Job {
+    int32_t n, r;
+    int64_t out_off;   // complex elements into the destination store
+};
+
+struct StepIIArgs {
+    const Group *groups;
+    const Segment *segs;
+    const Item *items;
+    const int64_t *doff;     // [kMaxLevels][nz+1][kMaxRings]
+    int nz1;
+    int64_t x_chunk;
+    int tx;                  // x points per shared-memory tile
+    double *partials;
+};
+
+// --- launch helpers (kernels.cu); all return cudaGetLastError() --------------
+
+// z pass of the forward 3D transform: real rows of length ng -> kept
+// frequencies [0, nkeep) written transposed as out[k][row].
+template <typename R>
+cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
+                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s);
+
+// Batched row transforms written transposed: in[b][nrow][M] -> out[b][M][nrow]
+// (out at out_off[b] when out_off is not null, else b * M * nrow), times
+// scale; zero_dc clears element [0][0] of batch 0.
+template <typename R>
+cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
+                              int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
+                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s);
+
+// Step I, first pass: ring r of plane n of Delta (planes [nz+1][ng][ng]),
+// folded onto the M x M grid, transformed along u_y, written transposed to
+// gt[job][y_y][i].  unit = true uses Delta = 1 (the unit fields of Eq. 2FT).
+template <typename R>
+cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings,
+                               const Job *jobs, int64_t njobs, int M, bool unit,
+                               typename Cx<R>::T *gt, const typename Cx<R>::T *tw, int lg_tw,
+                               cudaStream_t s);
+
+// Step II: partial triple sums of every item (A: sums over one shared-memory
+// tile, S: block sums over the item's chunk).
+template <typename R, typename A, typename S>
+cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t nitems,
+                         size_t smem, cudaStream_t s);
+
+// S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
+template <typename A>
+cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const double *partials,
+                                   int ng, double *S, cudaStream_t s);
+
+// Binning epilogue of Eq. bs_lm2_1.  mode 0: B = sqrt((2l+1)/4pi) num /
+// (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
+template <typename W>
+cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
+                            const double *value, int l_max, const double *den, double norm,
+                            double *out, cudaStream_t s);
+
+// Y_lm normalisations nlm[l][m] and the prefactors sqrt((2l+1)/(4 pi)).
+cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);
+
+// N_tri of unordered ring triples from the unit fields (Eq. Ntri2), FP64.
+cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32_t *triples,
+                        int64_t ntriples, double *raw, cudaStream_t s);
+
+// Sizes of dynamic shared memory (bytes) of the transform kernels.
+size_t fft_rows_per_block(int M, size_t elem);
+
+}  // namespace bisp

@@ -1,0 +1,132 @@
+// plan.hpp -- host-side plan of the bispectrum-multipole estimator: ring
+// table, combination enumeration, work decomposition and table layouts.
+// Internal to libbisp; the public interface is include/bisp.h.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "bisp.h"
+
+namespace bisp {
+
+constexpr int kMaxRings = 64;     // N_r for N_g <= 1024 is 52
+constexpr int kMaxLevels = 11;    // reduction grids M = 2^3 .. 2^10
+constexpr int kMinLog2M = 3;      // smallest reduction grid, 8 x 8
+constexpr int kSegLen = 8;        // r3 values per Step-II segment
+
+// Ring table (Sec. II, implementation paragraph): ring r holds the modes
+// u = (i, j) with e_{r} <= |u| < e_{r+1}; e_0 = 0, widths 2^floor(r/10)
+// (0-based r), the outer edge capped at N_g/3.  Edges are kept as 3 e_r,
+// exact integers, so membership is the integer test
+// (3 e_r)^2 <= 9 |u|^2 < (3 e_{r+1})^2.
+struct Rings {
+    int ng = 0, nr = 0, nz = 0;        // nz = floor(N_g/3): planes 0..nz
+    int64_t e3[kMaxRings + 1] = {};
+    double kperp[kMaxRings] = {};      // mode-averaged |u|, grid units
+    int64_t count[kMaxRings] = {};
+    int maxc[kMaxRings] = {};          // largest |u_x| of a member (= largest |u_y|)
+};
+
+// Plane pair (n1, n2, n3 = -n1 - n2) on one reduction grid M: the set of
+// ring triples whose triple sum runs on the M x M grid.
+struct Group {
+    int32_t n1, n2, n3;        // signed planes
+    int32_t log2m;             // reduction grid M = 2^log2m
+    int32_t seg0, nseg;        // segments of this group
+    int64_t c0;                // index of the first combination (S order)
+    int32_t ncombo;
+    int32_t nchunk;            // x chunks of the M^2 grid
+    int32_t rlo[3], rhi[3];    // ring ranges staged for planes 1, 2, 3
+    int32_t self_conj;         // 1 for n1 = n2 = 0 (counted once), else 0
+    int64_t part0;             // partial sums [nchunk][ncombo] start here
+};
+
+// A run of up to kSegLen combinations (r1, r2, r3a + j), j < n, sharing the
+// product D(r1, n1) D(r2, n2).  coff is the offset of the run's first
+// combination inside its group.
+struct Segment {
+    uint8_t r1, r2, r3a, n;
+    int32_t coff;
+};
+
+// One Step-II launch unit: a chunk of the x grid of a group.
+struct Item {
+    int32_t group;
+    int32_t chunk;
+};
+
+// Per-combination data of the binning epilogue, in (k1, mu, t)-bin order.
+struct Record {
+    int32_t s_index;           // index into the S array (S order)
+    int32_t flags;             // bit 0: counted once (self-conjugate pair);
+                               // bit 1: linear triangle (azimuth averaged)
+    double pz;                 // cos(theta) of p (Eq. orient)
+    double cphi;               // cos(phi) of p
+};
+
+struct Level {
+    int log2m = 0;
+    int64_t njobs = 0;         // stored (plane, ring) fields on this grid
+    int64_t dstore_off = 0;    // first element of this grid in the D store
+};
+
+// Everything the host knows about a plan.
+struct HostPlan {
+    bisp_desc desc{};
+    std::vector<double> k1_edges;
+    Rings rings;
+    int n_lm = 0;
+    int64_t n_bins = 0;
+    double kf = 0, volume = 0;
+
+    // triangle counts N_tri[r1][r2][r3]
+    std::vector<int64_t> ntri;
+
+    // combinations in S order
+    std::vector<Group> groups;
+    std::vector<Segment> segs;
+    std::vector<Item> items;
+    int64_t n_combos = 0;
+    int64_t n_partials = 0;
+    int64_t n_pairs = 0;
+    double triple_products = 0;
+    std::vector<int32_t> combo_ints;    // [n_combos][6]  n1 n2 n3 r1 r2 r3
+    std::vector<int64_t> combo_ntri;
+    std::vector<int32_t> combo_bin;
+    std::vector<int32_t> combo_grid;
+    std::vector<Record> records_s;      // S order (moved to bin order later)
+    std::vector<double> ntri_s;         // N_tri per combination, S order
+
+    // bin-sorted records
+    std::vector<Record> records;
+    std::vector<double> rec_ntri;
+    std::vector<int64_t> bin_start;     // n_bins + 1
+
+    // D store: offset (in complex elements) of field (level, plane, ring),
+    // -1 where not stored; [kMaxLevels][nz+1][kMaxRings]
+    std::vector<int64_t> doff;
+    std::vector<Level> levels;          // levels in use
+    int64_t dstore_elems = 0;
+    int64_t gt_elems = 0;               // largest per-level Step-I scratch
+};
+
+// Build the ring table; returns false for an unsupported N_g.
+bool build_rings(int ng, Rings &R);
+
+// Reduction grid of a ring triple: the smallest power of two M >= 8 with
+// M > maxc1 + maxc2 + maxc3, capped at N_g.  On that grid no non-zero sum
+// u + v + w of members aliases to zero, so the triple sum over x on the
+// M x M grid is exactly (M/N_g)^2 times the sum on the N_g x N_g grid.
+int triple_log2m(const Rings &R, int r1, int r2, int r3);
+
+// Enumerate the accepted combinations of one half of the plane pairs and
+// fill groups, segments, items, records, combination tables and the D-store
+// layout.  Requires rings and ntri.  Returns "" or an error message.
+std::string enumerate(HostPlan &P, int64_t x_chunk);
+
+// Counting sort of the records by (k1, mu, t) bin.
+void sort_records(HostPlan &P);
+
+}  // namespace bisp

@@ -1,0 +1,187 @@
+"""GPU parity of the CUDA estimator against the FP64 oracle.
+
+Every check calls the CUDA library through its C ABI (``paper_2405_14513_gb300.api``)
+on seeded synthetic fields and compares with the oracle on the same input:
+the transformed planes (forward transform), the D fields of Step I on each
+reduction grid (Eq. iFT), the combination table and its triangle counts
+(Eqs. Ntri1/Ntri2), the per-combination sums (Eq. fftbs), the denominators
+and the multipoles of Eq. bs_lm2_1.
+
+Tolerances: relative error of B_l^m per bin, floored at 1e-2 of the largest
+|B_l^m| of that moment (moments that change sign pass through zero), is at
+most 1e-4 for the FP32-transform paths and 1e-10 for the FP64 path.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2405_14513_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2405_14513_gb300 import api  # noqa: E402
+
+TOL = {"fp32": 1e-4, "mixed": 1e-4, "fp64": 1e-10}
+
+
+def floored_rel_err(got, ref):
+    """max over bins of |got - ref| / max(|ref|, 1e-2 max_bins |ref|), per moment."""
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(got)), "empty-bin pattern differs"
+    g = np.where(fin, got, 0.0).reshape(-1, ref.shape[-1])
+    r = np.where(fin, ref, 0.0).reshape(-1, ref.shape[-1])
+    floor = 1e-2 * np.abs(r).max(axis=0, keepdims=True)
+    return (np.abs(g - r) / np.maximum(np.abs(r), np.maximum(floor, 1e-300))).max(axis=0)
+
+
+class Case:
+    def __init__(self, ng, L, n_k1, nmu, nt, l_max, seed=1, precision="mixed", edges=None):
+        self.ng, self.L, self.nmu, self.nt, self.l_max = ng, L, nmu, nt, l_max
+        self.edges = synth.default_k1_edges(ng, L, n_k1) if edges is None else np.asarray(edges)
+        self.precision = precision
+        field = synth.make_field(ng, L, seed)
+        dt = np.float64 if precision == "fp64" else np.float32
+        self.field = field.astype(dt)                     # what the GPU sees
+        self.field64 = self.field.astype(np.float64)      # the same values for the oracle
+        self.plan = api.Plan(ng, L, self.edges, nmu, nt, l_max, precision=precision, max_batch=2)
+        self.ws = self.plan.workspace(2)
+        d = torch.from_numpy(self.field).cuda()
+        self.B = self.plan.estimate(d, self.ws).cpu().numpy()[0]
+        torch.cuda.synchronize()
+        self._oracle = None
+
+    @property
+    def oracle(self):
+        if self._oracle is None:
+            self._oracle = O.estimate(self.field64, self.L, self.edges, self.nmu, self.nt, self.l_max)
+        return self._oracle
+
+
+@pytest.fixture(scope="module")
+def c64():
+    # 64^3, L = 1000 Mpc/h, 6 linear k1 bins, (mu, t) step 0.1, l <= 6
+    return Case(64, 1000.0, 6, 5, 5, 6)
+
+
+@pytest.fixture(scope="module")
+def c64_fp64():
+    return Case(64, 1000.0, 6, 5, 5, 6, precision="fp64")
+
+
+def test_forward_transform_planes(c64):
+    cube = O.forward(c64.field64, c64.L)
+    nz = c64.ng // 3
+    for n in (0, 1, 7, nz):
+        got = c64.plan.delta_plane(c64.ws, n)
+        want = cube[:, :, n]
+        assert np.abs(got - want).max() < 2e-6 * np.abs(want).max()
+
+
+def test_step1_dfields_on_every_grid(c64):
+    tab = c64.plan.combo_table()
+    rng = np.random.default_rng(3)
+    seen = set()
+    for k in rng.choice(len(tab["ints"]), size=60, replace=False):
+        n1, n2, n3, r1, r2, r3 = tab["ints"][k]
+        M = int(tab["grid"][k])
+        for n, r in ((n1, r1), (n2, r2), (n3, r3)):
+            key = (M, abs(int(n)), int(r))
+            if key in seen:
+                continue
+            seen.add(key)
+            got = c64.plan.dfield(c64.ws, M, abs(int(n)), int(r))
+            full = O.dfield(c64.field64, c64.L, int(r), abs(int(n)))
+            step = c64.ng // M
+            want = full[::step, ::step]
+            assert np.abs(got - want).max() < 2e-6 * max(np.abs(want).max(), 1e-30), key
+
+
+def test_combination_table_matches_oracle(c64):
+    tab = c64.plan.combo_table()
+    ref = O.combos(c64.ng, c64.L, c64.edges, c64.nmu, c64.nt, half_space=True)
+    key = lambda ints: [tuple(r) for r in ints]
+    g = dict(zip(key(tab["ints"]), zip(tab["ntri"], tab["bin"])))
+    o = dict(zip(key(ref["ints"]), zip(ref["ntri"], ref["bin"])))
+    assert set(g) == set(o)
+    for k, v in o.items():
+        assert g[k] == (v[0], v[1]), k
+
+
+def test_denominators_match_oracle(c64):
+    den = c64.plan.denominator()
+    ref = O.select_even(c64.oracle["den"], c64.l_max)
+    assert np.abs(den - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("which", ["mixed", "fp64"])
+def test_per_combination_sums(which, c64, c64_fp64):
+    """Re S of Eq. fftbs per combination.  FP32 transforms carry about 1e-6
+    relative error per field value, so the FP32-path bound is 1e-4 of the
+    rms sum; the FP64 path is held to 1e-10."""
+    c = c64 if which == "mixed" else c64_fp64
+    tab = c.plan.combo_table()
+    S = c.plan.combo_sums(c.ws)
+    rng = np.random.default_rng(5)
+    pick = rng.choice(len(S), size=400, replace=False)
+    want = O.combo_sums(c.field64, c.L, tab["ints"][pick]).real
+    scale = np.sqrt(np.mean(want ** 2))
+    assert np.abs(S[pick] - want).max() < TOL[which] * scale
+
+
+@pytest.mark.parametrize("which", ["mixed", "fp64"])
+def test_multipoles_match_oracle(which, c64, c64_fp64):
+    c = c64 if which == "mixed" else c64_fp64
+    ref = O.select_even(c.oracle["B"], c.l_max)
+    err = floored_rel_err(c.B, ref)
+    assert err.max() < TOL[which], err
+
+
+def test_fp32_plain_path():
+    c = Case(64, 1000.0, 6, 5, 5, 6, precision="fp32", seed=2)
+    ref = O.select_even(c.oracle["B"], c.l_max)
+    err = floored_rel_err(c.B, ref)
+    assert err.max() < TOL["fp32"], err
+
+
+def test_brute_force_16():
+    """N_g = 16 against the direct triangle sums of Eq. binbs / Eq. Ntri1."""
+    c = Case(16, 1000.0, 2, 5, 5, 6, precision="fp64", seed=4)
+    ref = O.estimate(c.field64, c.L, c.edges, c.nmu, c.nt, c.l_max, direct=True)
+    err = floored_rel_err(c.B, O.select_even(ref["B"], c.l_max))
+    assert err.max() < TOL["fp64"], err
+
+
+def test_batch_equals_single_calls(c64):
+    f2 = synth.make_field(64, 1000.0, 9).astype(np.float32)
+    d = torch.from_numpy(np.stack([c64.field, f2])).cuda()
+    both = c64.plan.estimate(d, c64.ws).cpu().numpy()
+    one = c64.plan.estimate(torch.from_numpy(f2).cuda()[None], c64.ws).cpu().numpy()[0]
+    assert np.array_equal(both[0], c64.B, equal_nan=True)
+    assert np.array_equal(both[1], one, equal_nan=True)
+
+
+def test_host_entry_point_matches_device(c64):
+    host = c64.plan.estimate_host(c64.field)[0]
+    assert np.array_equal(host, c64.B, equal_nan=True)
+
+
+def test_ragged_and_degenerate_configurations():
+    """Smallest grid, a single k1 bin, l_max = 0, one (mu, t) bin and k1
+    edges that leave bins empty."""
+    for ng, L, edges, nmu, nt, lmax in [
+        (8, 100.0, None, 1, 1, 0),
+        (32, 500.0, np.array([0.03, 0.1, 0.12]), 3, 7, 2),
+        (32, 500.0, synth.default_k1_edges(32, 500.0, 1), 16, 16, 8),
+    ]:
+        if edges is None:
+            edges = synth.default_k1_edges(ng, L, 1)
+        c = Case(ng, L, len(edges) - 1, nmu, nt, lmax, precision="fp64", edges=edges, seed=6)
+        ref = O.select_even(c.oracle["B"], lmax)
+        if np.isfinite(ref).any():
+            assert floored_rel_err(c.B, ref).max() < TOL["fp64"]
+        else:
+            assert not np.isfinite(c.B).any()
