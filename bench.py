@@ -1,0 +1,330 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 estimator of the redshift-space bispectrum
+multipoles B_l^m(k1, mu, t) on its headline workload.
+
+Workload: N_g = 512, L = 2000 Mpc/h, 30 linear k1 bins over
+[(N_g/12) k_f, (N_g/3) k_f], (mu, t) step 0.025 on [0.5, 1] (20 x 20 bins),
+l <= 6 (16 moments), FP32 transforms and products with FP64 sums ("mixed").
+The input is the seeded synthetic non-Gaussian redshift-space field (P(k) =
+A k^-2, sigma_G = 0.1, f_NG = 0.5, Kaiser beta = 0.5).
+
+One step = one full estimate of one field (forward transform, Step I,
+Step II, binning).  The metric is output (k1, mu, t) bins per second, each
+bin carrying all 16 moments ("configs/s").  Each rank estimates its own
+field (independent problems, no collective in the data path): value is
+(ranks x bins) / max-over-ranks time, "scaling": "weak".
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle (the only other implementation
+of the method; the paper publishes no code) on a bounded sample of the same
+workload, on the host cores, and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NG, BOX, NK1, NMU, LMAX = 512, 2000.0, 30, 20, 6
+SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+METRIC = "B_l^m(k1,mu,t) configs/s at N_g=512"
+
+
+def workload(ng):
+    from paper_2405_14513_gb300 import synth
+    return {"workload": f"redshift-space bispectrum multipoles, N_g={ng}^3, L={BOX:g} Mpc/h, "
+                        f"{NK1} linear k1 bins, (mu,t) step 0.025 ({NMU}x{NMU}), l<=6 (16 moments)",
+            "n_g": ng, "box_len": BOX, "n_k1": NK1, "n_mu": NMU, "n_t": NMU, "l_max": LMAX,
+            "precision": "mixed (FP32 transforms/products, FP64 sums)",
+            "field": "seeded synthetic: P=A k^-2, sigma_G=0.1, f_NG=0.5, Kaiser beta=0.5",
+            "l2": "inputs and D-field store larger than L2 (no flush needed)"}, \
+        synth.default_k1_edges(ng, BOX, NK1)
+
+
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=None):
+        self.rows, self.proc = [], None
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if index is not None:
+            cmd += ["-i", str(index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _traffic(ng):
+    """DRAM bytes per Step-II launch from the committed ncu summary, if any."""
+    p = os.path.join(ROOT, "profiles", "step2_dram.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        if d.get("kernel_digest") != _kernel_digest():
+            return None
+        return float(d["bytes_per_launch"]) * float(d.get("scale_to_ng", {}).get(str(ng), 1.0))
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+def _kernel_digest():
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2405_14513_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+# ----------------------------------------------------------------------------
+def oracle_table(ng, edges):
+    """The oracle's combination table (its own triangle counts, Eq. Ntri2) and its wall time."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    c = O.combos(ng, BOX, edges, NMU, NMU, half_space=True, nthreads=os.cpu_count() or 1)
+    return c, time.perf_counter() - t0
+
+
+def cpu_baseline(ng, edges, field64, n_bins, sample_pairs=2, seed=0, table=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload.
+
+    The oracle enumerates the combinations (its own triangle counts, Eq.
+    Ntri2), then computes the plane transforms, D fields and triple sums of
+    every combination of `sample_pairs` random plane pairs.  Its full-workload
+    time is extrapolated stage by stage: table time + plane time + per-field
+    time x all (plane, ring) fields + per-combination time x all
+    combinations of both signs of n (the oracle enumerates both)."""
+    from oracle import oracle as O
+    nthreads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    c, t_tab = table if table is not None else oracle_table(ng, edges)
+    ints = c["ints"]
+    n_half = len(ints)
+    n_self = int(np.sum((ints[:, 0] == 0) & (ints[:, 1] == 0)))
+    n_full = 2 * n_half - n_self
+    key = ints[:, 0].astype(np.int64) * 4096 + ints[:, 1]      # combinations come grouped by pair
+    starts = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    pairs = ints[starts, :2]
+    rng = np.random.default_rng(seed)
+    pick = pairs[rng.choice(len(pairs), size=min(sample_pairs, len(pairs)), replace=False)]
+    pk = set(int(p[0]) * 4096 + int(p[1]) for p in pick)
+    sample = np.concatenate([ints[a:b] for a, b in zip(starts, np.r_[starts[1:], n_half])
+                             if int(key[a]) in pk])
+    times = []
+    O.combo_sums(field64, BOX, sample, nthreads=nthreads, times=times)
+    t_planes, t_fields, t_sums = times
+    nr = len(O.rings(ng)[1])
+    nz = ng // 3
+    fields = {(int(n), int(r)) for row in sample for n, r in zip(row[:3], row[3:])}
+    t_full = (t_tab + t_planes + t_fields / len(fields) * (2 * nz + 1) * nr
+              + t_sums / len(sample) * n_full)
+    return {"value": n_bins / t_full, "unit": "configs/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"oracle table of all {n_half} combinations ({t_tab:.1f} s), then plane transforms, "
+                      f"{len(fields)} D fields and {len(sample)} triple sums of {len(pick)} random plane "
+                      f"pairs; full time extrapolated per stage to {(2 * nz + 1) * nr} fields and "
+                      f"{n_full} combinations: {t_full:.0f} s",
+            "wall_s": time.perf_counter() - t0 + (t_tab if table is None else 0.0), "extrapolated_s": t_full}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    from paper_2405_14513_gb300 import synth
+    ng = args.ng
+    cfg, edges = workload(ng)
+    n_bins = NK1 * NMU * NMU
+    field64 = synth.make_field(ng, BOX, 1).astype(np.float32).astype(np.float64)
+    vals, walls = [], []
+    table = oracle_table(ng, edges)
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(ng, edges, field64, n_bins, sample_pairs=1, seed=i, table=table)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            walls.append(r["wall_s"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "configs/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": n_bins / value * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "value": value, "unit": "configs/s",
+                             "sample": "each step: " + r["sample"]},
+            "e2e": {"value": value, "unit": "configs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s_per_step": statistics.median(walls)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2405_14513_gb300 import api, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    ng = args.ng
+    cfg, edges = workload(ng)
+    plan = api.Plan(ng, BOX, edges, NMU, NMU, LMAX, precision="mixed", max_batch=1)
+    field = synth.make_field_torch(ng, BOX, 1 + rank, device=dev).to(torch.float32).contiguous()
+    ws = plan.workspace(1, device=dev)
+    out = torch.empty(plan.out_shape(1), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        plan.estimate(field, ws, out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    plan.set_timing(True)
+    clocks = ClockSampler(index=local) if rank == 0 else None
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        plan.estimate(field, ws, out=out, stream=stream)
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop() if clocks else None
+    ms = t0.elapsed_time(t1) / args.steps
+    st_ms, st_n = plan.stage_times()
+    plan.set_timing(False)
+    flops = plan.stage_flops()
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * plan.n_bins / (ms / 1e3)
+    finite = bool(torch.isfinite(out).any().item())
+
+    # end to end through the host entry point: pinned field in, B out, copies timed
+    host = field.cpu().pin_memory()
+    host_np = host.numpy()
+    out_h = torch.empty(plan.out_shape(1), dtype=torch.float64).pin_memory().numpy()
+    plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
+    barrier()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
+    te = (time.perf_counter() - te) / args.steps
+    if world > 1:
+        t = torch.tensor([te], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e = {"value": world * plan.n_bins / te, "unit": "configs/s",
+           "h2d_bytes_per_step": int(host.numel() * host.element_size()),
+           "d2h_bytes_per_step": int(out_h.size * 8)}
+
+    # roofline of the dominant kernel (Step II), from its own events
+    # Step II runs as one launch per block class; its time per estimate is the
+    # sum of those launches, timed by events on the launching stream
+    s2_ms = st_ms["step2"] / args.steps
+    achieved = flops["step2"] / (s2_ms / 1e3) / 1e12
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    roof = {"kernel": "k_step2 (Step II triple sums)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(ng),
+            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
+            "flops_per_estimate": flops["step2"], "ms_per_estimate": s2_ms,
+            "launches_per_estimate": st_n["step2"] / args.steps}
+    stage_share = {k: st_ms[k] / max(sum(st_ms.values()), 1e-9) for k in st_ms}
+    launches = int(sum(st_n.values()))
+
+    line = {"metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
+            "e2e": e2e, "roofline": roof, "gpu_launches": launches, "clocks": clk,
+            "stage_ms_per_step": {k: v / args.steps for k, v in st_ms.items()},
+            "stage_share": stage_share, "output_finite": finite,
+            "plan": {k: plan.info[k] for k in ("n_combos", "n_pairs", "n_items", "n_levels",
+                                                "triple_products", "dstore_bytes", "workspace_bytes")}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        f64 = field.double().cpu().numpy()
+        del ws
+        torch.cuda.empty_cache()
+        line["cpu_baseline"] = cpu_baseline(ng, edges, f64, plan.n_bins)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ng", type=int, default=NG, help="grid size (the headline workload is 512)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,7 +84,7 @@ typedef struct {
     int64_t n_bins;                  /* n_k1 n_mu n_t                                 */
     int64_t n_combos;                /* accepted combinations, one of each +-n pair   */
     int64_t n_pairs;                 /* plane pairs (n1, n2) with a combination       */
-    int64_t n_items;                 /* Step-II work items (pair, grid, x chunk)      */
+    int64_t n_items;                 /* Step-II blocks (pair, grid, x chunk, tiles)   */
     double triple_products;          /* sum over combinations of grid points summed   */
     size_t dstore_bytes;             /* D-field store of one field                    */
     size_t workspace_bytes;          /* estimator_workspace_bytes(plan, 1)            */
@@ -133,6 +133,36 @@ const char *estimator_status_string(int status);
 
 /* Description of the last failure on the calling thread ("" if none). */
 const char *estimator_last_error(void);
+
+/* ---------------- stage timing ---------------- */
+
+/* Stages timed by estimator_stage_times. */
+typedef enum {
+    BISP_STAGE_FORWARD = 0,   /* forward 3D transform (z, y, x passes)          */
+    BISP_STAGE_STEP1 = 1,     /* ring-masked 2D transforms on each grid (Eq. iFT) */
+    BISP_STAGE_STEP2 = 2,     /* triple-product reduction (Eq. fftbs)            */
+    BISP_STAGE_REDUCE = 3,    /* partial sums -> per-combination sums            */
+    BISP_STAGE_BIN = 4,       /* Y_lm weighting, binning, ratio (Eq. bs_lm2_1)   */
+    BISP_N_STAGES = 5
+} bisp_stage;
+
+/* Switch per-stage timing on (1) or off (0) for the following estimates.
+ * When on, every estimate records CUDA events on its stream around each
+ * stage (one event pair per stage and field).  Switching on clears the
+ * totals. */
+int estimator_set_timing(bisp_plan *plan, int on);
+
+/* Totals since timing was switched on: ms[BISP_N_STAGES] elapsed time per
+ * stage (CUDA events, device clock), launches[BISP_N_STAGES] kernels
+ * launched per stage.  HOST pointers; either may be NULL.  Waits for the
+ * recorded events. */
+int estimator_stage_times(bisp_plan *plan, double *ms, int64_t *launches);
+
+/* Algorithmic floating-point operations of one estimate of one field, per
+ * stage (HOST pointer flops[BISP_N_STAGES]): for Step II, 4 per grid point of
+ * each combination (Re of a complex product, two FMAs) plus 6 per grid
+ * point of each distinct (plane pair, grid, r1, r2) product D1 D2. */
+int estimator_stage_flops(const bisp_plan *plan, double *flops);
 
 /* ---------------- introspection, for tests and diagnostics ---------------- */
 

@@ -351,9 +351,11 @@ static double ntri_fft(const rings_t *R, long *table)
     cplx *If = malloc(sizeof(cplx) * (size_t)nr * np);
     for (int r = 0; r < nr; ++r) ifield(R, r, If + r * np);
     double worst = 0;
+    /* N_tri is symmetric in its three rings: evaluate r1 <= r2 <= r3 only */
 #pragma omp parallel for schedule(dynamic) reduction(max : worst)
     for (long t = 0; t < (long)nr * nr * nr; ++t) {
         int r1 = (int)(t / ((long)nr * nr)), r2 = (int)((t / nr) % nr), r3 = (int)(t % nr);
+        if (!(r1 <= r2 && r2 <= r3)) continue;
         const cplx *a = If + r1 * np, *b = If + r2 * np, *c = If + r3 * np;
         cplx s = 0;
         for (long x = 0; x < np; ++x) s += a[x] * b[x] * c[x];
@@ -361,7 +363,8 @@ static double ntri_fft(const rings_t *R, long *table)
         double rv = nearbyint(v);
         double res = fabs(v - rv) + fabs(cimag(s)) / (double)np;
         if (res > worst) worst = res;
-        table[t] = (long)rv;
+        const int p[6][3] = {{r1, r2, r3}, {r1, r3, r2}, {r2, r1, r3}, {r2, r3, r1}, {r3, r1, r2}, {r3, r2, r1}};
+        for (int q = 0; q < 6; ++q) table[((long)p[q][0] * nr + p[q][1]) * nr + p[q][2]] = (long)rv;
     }
     free(If);
     return worst;
@@ -761,9 +764,12 @@ long bo_combos(const bo_desc *d, int half_space, long cap, int *ints, long *ntri
 /* ------------------------------------------------------------------------ */
 /* Sums S = sum_x D1 D2 D3 (Eq. fftbs) for a given list of combinations,     */
 /* computing only the planes and D fields the list needs.  ints[k][6] as in  */
-/* bo_combos.  S_re_im[k][2].  For spot checks at large N_g.                 */
+/* bo_combos.  S_re_im[k][2].  For spot checks at large N_g.  times (may be  */
+/* NULL) gets the wall seconds of the three stages: [0] the needed planes of */
+/* the forward transform, [1] the D fields, [2] the triple sums.             */
 /* ------------------------------------------------------------------------ */
-int bo_combo_sums(int ng, double box_len, const double *delta, long nc, const int *ints, int nthreads, double *S_re_im)
+int bo_combo_sums(int ng, double box_len, const double *delta, long nc, const int *ints, int nthreads,
+                  double *S_re_im, double *times)
 {
     set_threads(nthreads);
     rings_t R;
@@ -771,38 +777,52 @@ int bo_combo_sums(int ng, double box_len, const double *delta, long nc, const in
     int nr = R.nr, nz = R.nz;
     long np = (long)ng * ng;
     long nfield = (long)(2 * nz + 1) * nr;
+    for (long k = 0; k < nc; ++k)
+        for (int s = 0; s < 3; ++s) {
+            int n = ints[6 * k + s], r = ints[6 * k + 3 + s];
+            if (n < -nz || n > nz || r < 0 || r >= nr) { free(R.ringidx); return -1; }
+        }
     cplx **D = calloc((size_t)nfield, sizeof(cplx *));
     char *need_plane = calloc((size_t)(2 * nz + 1), 1);
     char *need_field = calloc((size_t)nfield, 1);
     for (long k = 0; k < nc; ++k)
         for (int s = 0; s < 3; ++s) {
             int n = ints[6 * k + s], r = ints[6 * k + 3 + s];
-            if (n < -nz || n > nz || r < 0 || r >= nr) { free(D); free(need_plane); free(need_field); free(R.ringidx); return -1; }
             need_plane[n + nz] = 1;
             need_field[(long)(n + nz) * nr + r] = 1;
         }
-    /* planes: Delta(., ., n) = (V/N_g^3) 2D-DFT over (x,y) of sum_z delta exp(-2 pi i n z / N_g) */
+    double t0 = 0, t1 = 0, t2 = 0, t3 = 0;
+#ifdef _OPENMP
+    t0 = omp_get_wtime();
+#endif
+    /* planes: the DFT of every (x, y) column along z, kept at the needed n,
+     * then (V/N_g^3) times the 2D DFT over (x, y) */
     double V = box_len * box_len * box_len, scale = V / ((double)np * ng);
     cplx **plane = calloc((size_t)(2 * nz + 1), sizeof(cplx *));
-    for (int pi = 0; pi < 2 * nz + 1; ++pi) {
-        if (!need_plane[pi]) continue;
-        int n = pi - nz;
-        cplx *p = malloc(sizeof(cplx) * (size_t)np);
-#pragma omp parallel for schedule(static)
+    for (int pi = 0; pi < 2 * nz + 1; ++pi)
+        if (need_plane[pi]) plane[pi] = malloc(sizeof(cplx) * (size_t)np);
+#pragma omp parallel
+    {
+        cplx *col = malloc(sizeof(cplx) * (size_t)ng), *tmp = malloc(sizeof(cplx) * (size_t)ng);
+#pragma omp for schedule(static)
         for (long xy = 0; xy < np; ++xy) {
-            cplx s = 0;
-            for (long z = 0; z < ng; ++z) {
-                long nzmod = (((long)n * z) % ng + ng) % ng;
-                double a = -BO_TWO_PI * (double)nzmod / (double)ng;
-                s += delta[xy * ng + z] * (cos(a) + I * sin(a));
-            }
-            p[xy] = s;
+            for (long z = 0; z < ng; ++z) col[z] = delta[xy * ng + z];
+            dft1(col, ng, tmp);
+            for (int pi = 0; pi < 2 * nz + 1; ++pi)
+                if (plane[pi]) plane[pi][xy] = col[((pi - nz) % ng + ng) % ng];
         }
-        dft2(p, ng);
-        for (long i = 0; i < np; ++i) p[i] *= scale;
-        if (n == 0) p[0] = 0;
-        plane[pi] = p;
+        free(col);
+        free(tmp);
     }
+    for (int pi = 0; pi < 2 * nz + 1; ++pi) {
+        if (!plane[pi]) continue;
+        dft2(plane[pi], ng);
+        for (long i = 0; i < np; ++i) plane[pi][i] *= scale;
+        if (pi == nz) plane[pi][0] = 0;
+    }
+#ifdef _OPENMP
+    t1 = omp_get_wtime();
+#endif
     for (long f = 0; f < nfield; ++f) {
         if (!need_field[f]) continue;
         int n = (int)(f / nr) - nz, r = (int)(f % nr);
@@ -814,6 +834,9 @@ int bo_combo_sums(int ng, double box_len, const double *delta, long nc, const in
         dft2(o, ng);
         D[f] = o;
     }
+#ifdef _OPENMP
+    t2 = omp_get_wtime();
+#endif
 #pragma omp parallel for schedule(dynamic)
     for (long k = 0; k < nc; ++k) {
         const int *q = ints + 6 * k;
@@ -825,6 +848,10 @@ int bo_combo_sums(int ng, double box_len, const double *delta, long nc, const in
         S_re_im[2 * k] = creal(s);
         S_re_im[2 * k + 1] = cimag(s);
     }
+#ifdef _OPENMP
+    t3 = omp_get_wtime();
+#endif
+    if (times) { times[0] = t1 - t0; times[1] = t2 - t1; times[2] = t3 - t2; }
     for (long f = 0; f < nfield; ++f) free(D[f]);
     for (int pi = 0; pi < 2 * nz + 1; ++pi) free(plane[pi]);
     free(plane);

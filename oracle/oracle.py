@@ -63,7 +63,7 @@ def _load():
             lib.bo_estimate.restype = C.c_long
             lib.bo_combos.argtypes = [C.POINTER(Desc), C.c_int, C.c_long, ip, lp, ip, dp]
             lib.bo_combos.restype = C.c_long
-            lib.bo_combo_sums.argtypes = [C.c_int, C.c_double, dp, C.c_long, ip, C.c_int, dp]
+            lib.bo_combo_sums.argtypes = [C.c_int, C.c_double, dp, C.c_long, ip, C.c_int, dp, dp]
             lib.bo_combo_sums.restype = C.c_int
             lib.bo_gauss_legendre.argtypes = [C.c_int, dp, dp]
             lib.bo_continuum.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.c_int, C.c_int,
@@ -203,14 +203,19 @@ def combos(ng, box_len, k1_edges, n_mu, n_t, l_max=0, half_space=True, direct=Fa
     return {"ints": ints[:n], "ntri": nt[:n], "bin": bins[:n], "geo": geo[:n]}
 
 
-def combo_sums(delta, box_len, ints, nthreads=0) -> np.ndarray:
-    """S = sum_x D1 D2 D3 (Eq. fftbs numerator) for listed combinations."""
+def combo_sums(delta, box_len, ints, nthreads=0, times=None) -> np.ndarray:
+    """S = sum_x D1 D2 D3 (Eq. fftbs numerator) for listed combinations.
+    If ``times`` is a list, the wall seconds of the plane transforms, the D
+    fields and the triple sums are appended to it."""
     d_arr = np.ascontiguousarray(delta, dtype=np.float64)
     ng = d_arr.shape[0]
     q = np.ascontiguousarray(ints, dtype=np.int32)
     out = np.zeros((len(q), 2))
-    if _load().bo_combo_sums(ng, box_len, _dp(d_arr), len(q), _ip(q), nthreads, _dp(out)):
+    t = np.zeros(3)
+    if _load().bo_combo_sums(ng, box_len, _dp(d_arr), len(q), _ip(q), nthreads, _dp(out), _dp(t)):
         raise ValueError("bad combination list")
+    if times is not None:
+        times.extend(t.tolist())
     return out[:, 0] + 1j * out[:, 1]
 
 

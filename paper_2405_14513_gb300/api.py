@@ -77,6 +77,12 @@ def load():
         lib.estimator_dfield.restype = C.c_int
         lib.estimator_delta_plane.argtypes = [vp, vp, C.c_int, dp, vp]
         lib.estimator_delta_plane.restype = C.c_int
+        lib.estimator_set_timing.argtypes = [vp, C.c_int]
+        lib.estimator_set_timing.restype = C.c_int
+        lib.estimator_stage_times.argtypes = [vp, dp, vp]
+        lib.estimator_stage_times.restype = C.c_int
+        lib.estimator_stage_flops.argtypes = [vp, dp]
+        lib.estimator_stage_flops.restype = C.c_int
         _lib = lib
         return lib
 
@@ -221,6 +227,27 @@ class Plan:
         _check(load().estimator_delta_plane(self._h, C.c_void_p(workspace.data_ptr()), n, _dp(out),
                                             _stream_handle(stream)), "estimator_delta_plane")
         return out[..., 0] + 1j * out[..., 1]
+
+
+    # ------------------------------------------------------------------
+    def set_timing(self, on: bool):
+        _check(load().estimator_set_timing(self._h, 1 if on else 0), "estimator_set_timing")
+
+    def stage_times(self):
+        """(ms, launches) per stage since timing was switched on."""
+        ms = np.zeros(len(STAGES))
+        n = np.zeros(len(STAGES), dtype=np.int64)
+        _check(load().estimator_stage_times(self._h, _dp(ms), C.c_void_p(n.ctypes.data)),
+               "estimator_stage_times")
+        return dict(zip(STAGES, ms.tolist())), dict(zip(STAGES, n.tolist()))
+
+    def stage_flops(self):
+        f = np.zeros(len(STAGES))
+        _check(load().estimator_stage_flops(self._h, _dp(f)), "estimator_stage_flops")
+        return dict(zip(STAGES, f.tolist()))
+
+
+STAGES = ["forward", "step1", "step2", "reduce", "bin"]
 
 
 def status_string(status: int) -> str:

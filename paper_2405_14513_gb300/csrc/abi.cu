@@ -35,8 +35,7 @@ int fail(int code, const std::string &msg)
     } while (0)
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int64_t kXChunk = 65536;        // grid points of one Step-II item
-constexpr size_t kStep2SmemBudget = 200 * 1024;
+constexpr int64_t kXChunk = 16384;        // grid points of one Step-II unit
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -55,8 +54,8 @@ struct bisp_plan {
     size_t celem = 8;                    // bytes of one complex field value
     std::vector<void *> owned;           // device allocations of the plan
     Group *d_groups = nullptr;
-    Segment *d_segs = nullptr;
-    Item *d_items = nullptr;
+    Tile *d_tiles = nullptr;
+    Unit *d_units = nullptr;
     int64_t *d_doff = nullptr;
     Record *d_rec = nullptr;
     int64_t *d_bin_start = nullptr;
@@ -69,12 +68,17 @@ struct bisp_plan {
     std::vector<Job *> d_jobs;           // per level in use
     std::vector<int64_t *> d_job_off;    // per level: output offsets of the jobs
     size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, ws_bytes = 0;
-    int tx = 0;
-    size_t step2_smem = 0;
     size_t resident = 0;
     // buffers of estimator_estimate_host
     void *own_ws = nullptr, *own_in = nullptr;
     double *own_out = nullptr;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Mark { int stage; cudaEvent_t a, b; int launches; };
+    std::vector<Mark> pending;
+    double stage_ms[BISP_N_STAGES] = {};
+    int64_t stage_launches[BISP_N_STAGES] = {};
 };
 
 namespace {
@@ -105,9 +109,61 @@ int upload(bisp_plan *p, T **out, const std::vector<T> &v, cudaStream_t s)
     return BISP_OK;
 }
 
+cudaEvent_t take_event(bisp_plan *p)
+{
+    if (!p->ev_pool.empty()) {
+        cudaEvent_t e = p->ev_pool.back();
+        p->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Event pair around one stage on stream s, when timing is on.
+struct StageMark {
+    bisp_plan *p;
+    int stage, launches;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    StageMark(bisp_plan *p_, int stage_, int launches_, cudaStream_t s_) : p(p_), stage(stage_), launches(launches_), s(s_)
+    {
+        if (p->timing && (a = take_event(p))) cudaEventRecord(a, s);
+    }
+    ~StageMark()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(p);
+        if (!b) { p->ev_pool.push_back(a); return; }
+        cudaEventRecord(b, s);
+        p->pending.push_back(bisp_plan::Mark{stage, a, b, launches});
+    }
+};
+
+int collect_times(bisp_plan *p)
+{
+    for (auto &m : p->pending) {
+        CK(cudaEventSynchronize(m.b));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, m.a, m.b));
+        p->stage_ms[m.stage] += ms;
+        p->stage_launches[m.stage] += m.launches;
+        p->ev_pool.push_back(m.a);
+        p->ev_pool.push_back(m.b);
+    }
+    p->pending.clear();
+    return BISP_OK;
+}
+
 void free_plan(bisp_plan *p)
 {
     if (!p) return;
+    for (auto &m : p->pending) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     for (void *q : p->owned) cudaFree(q);
     if (p->own_ws) cudaFree(p->own_ws);
     if (p->own_in) cudaFree(p->own_in);
@@ -271,13 +327,15 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     }
     int st = compute_ntri(p, s);
     if (st) return st;
+    P.celem = p->celem;
+    P.max_cls = desc->precision == BISP_PREC_FP64 ? 3 : 4;   // FP64 blocks have at most 8 warps
     std::string err = enumerate(P, kXChunk);
     if (!err.empty()) return fail(BISP_INTERNAL, err);
     sort_records(P);
 
     st = upload(p, &p->d_groups, P.groups, s);
-    if (!st) st = upload(p, &p->d_segs, P.segs, s);
-    if (!st) st = upload(p, &p->d_items, P.items, s);
+    if (!st) st = upload(p, &p->d_tiles, P.tiles, s);
+    if (!st) st = upload(p, &p->d_units, P.units, s);
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
     if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
@@ -335,20 +393,6 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->off_part = o; o = align256(o + size_t(P.n_partials) * sizeof(double));
     p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
     p->ws_bytes = o;
-    // Step-II tile: the rings of three planes for TX points, plus block sums
-    int ncmax = 0, nsmax = 1;
-    for (const Group &G : P.groups) {
-        ncmax = std::max(ncmax, G.ncombo);
-        nsmax = std::max(nsmax, (G.rhi[0] - G.rlo[0] + 1) + (G.rhi[1] - G.rlo[1] + 1) + (G.rhi[2] - G.rlo[2] + 1));
-    }
-    const size_t ssum = desc->precision == BISP_PREC_FP32 ? sizeof(float) : sizeof(double);
-    const size_t fixed = ((size_t(ncmax) * ssum + 15) & ~size_t(15)) + size_t(nsmax) * 12 + 32;
-    if (fixed + size_t(nsmax) * 33 * p->celem > kStep2SmemBudget)
-        return fail(BISP_INTERNAL, "Step-II group too large for shared memory");
-    int tx = int((kStep2SmemBudget - fixed) / (size_t(nsmax) * p->celem)) - 1;
-    tx = std::min(512, tx - tx % 32);
-    p->tx = tx;
-    p->step2_smem = fixed + size_t(nsmax) * (tx + 1) * p->celem;
     CK(cudaStreamSynchronize(s));
     return BISP_OK;
 }
@@ -369,27 +413,38 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
     const int64_t ng2 = int64_t(ng) * ng;
     const R scale = R(P.volume / (double(ng2) * ng));
-    StepIIArgs a2{p->d_groups, p->d_segs, p->d_items, p->d_doff, Rg.nz + 1, kXChunk, p->tx, part};
+    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
     for (int b = 0; b < batch; ++b) {
         const R *d = delta + int64_t(b) * ng2 * ng;
-        // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
-        CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, p->lg_tw, s));
-        CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, p->lg_tw, s));
-        CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, p->lg_tw, s));
-        // Step I: D(r, n) on each reduction grid (Eq. iFT)
-        for (size_t l = 0; l < P.levels.size(); ++l) {
-            const Level &L = P.levels[l];
-            const int M = 1 << L.log2m;
-            CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, p->lg_tw, s));
-            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, p->lg_tw, s));
+        {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
+            StageMark m(p, BISP_STAGE_FORWARD, 3, s);
+            CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, p->lg_tw, s));
+            CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, p->lg_tw, s));
+            CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, p->lg_tw, s));
         }
-        // Step II: triple sums (Eq. fftbs)
-        CK((launch_step2<R, A, S>(a2, dstore, int64_t(P.items.size()), p->step2_smem, s)));
-        using RA = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
-        CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, s));
-        // binning and the ratio of Eq. bs_lm2_1
-        CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
-                              1.0 / (P.volume * double(ng2)), B + int64_t(b) * P.n_bins * P.n_lm, s));
+        {   // Step I: D(r, n) on each reduction grid (Eq. iFT)
+            StageMark m(p, BISP_STAGE_STEP1, int(2 * P.levels.size()), s);
+            for (size_t l = 0; l < P.levels.size(); ++l) {
+                const Level &L = P.levels[l];
+                const int M = 1 << L.log2m;
+                CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, p->lg_tw, s));
+                CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, p->lg_tw, s));
+            }
+        }
+        {   // Step II: triple sums (Eq. fftbs)
+            StageMark m(p, BISP_STAGE_STEP2, sizeof(R) == 8 ? 2 : 3, s);
+            CK(launch_step2<R>(a2, dstore, P.class_begin, s));
+        }
+        {
+            StageMark m(p, BISP_STAGE_REDUCE, 1, s);
+            using RA = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
+            CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, s));
+        }
+        {   // binning and the ratio of Eq. bs_lm2_1
+            StageMark m(p, BISP_STAGE_BIN, 1, s);
+            CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
+                                  1.0 / (P.volume * double(ng2)), B + int64_t(b) * P.n_bins * P.n_lm, s));
+        }
     }
     return BISP_OK;
 }
@@ -451,7 +506,7 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->n_bins = P.n_bins;
     info->n_combos = P.n_combos;
     info->n_pairs = P.n_pairs;
-    info->n_items = int64_t(P.items.size());
+    info->n_items = int64_t(P.units.size());
     info->triple_products = P.triple_products;
     info->dstore_bytes = size_t(P.dstore_elems) * p->celem;
     info->workspace_bytes = p->ws_bytes;
@@ -499,6 +554,48 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
 
 void estimator_destroy(bisp_plan *p) { free_plan(p); }
 
+int estimator_set_timing(bisp_plan *p, int on)
+{
+    if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    int st = collect_times(p);
+    if (st) return st;
+    p->timing = on != 0;
+    if (p->timing)
+        for (int i = 0; i < BISP_N_STAGES; ++i) { p->stage_ms[i] = 0; p->stage_launches[i] = 0; }
+    return BISP_OK;
+}
+
+int estimator_stage_times(bisp_plan *p, double *ms, int64_t *launches)
+{
+    if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    int st = collect_times(p);
+    if (st) return st;
+    for (int i = 0; i < BISP_N_STAGES; ++i) {
+        if (ms) ms[i] = p->stage_ms[i];
+        if (launches) launches[i] = p->stage_launches[i];
+    }
+    return BISP_OK;
+}
+
+int estimator_stage_flops(const bisp_plan *p, double *flops)
+{
+    if (!p || !flops) return fail(BISP_INVALID_ARG, "NULL argument");
+    const HostPlan &P = p->hp;
+    const double ng = P.desc.n_g, lg = ilog2i(P.desc.n_g), planes = P.rings.nz + 1;
+    // 5 N log2 N per complex transform of length N
+    flops[BISP_STAGE_FORWARD] = 5.0 * ng * lg * (ng * ng + 2.0 * planes * ng);
+    double s1 = 0;
+    for (const Level &L : P.levels) {
+        const double M = double(1 << L.log2m);
+        s1 += double(L.njobs) * 2.0 * M * 5.0 * M * L.log2m;
+    }
+    flops[BISP_STAGE_STEP1] = s1;
+    flops[BISP_STAGE_STEP2] = 4.0 * P.triple_products + 6.0 * P.pair_products;
+    flops[BISP_STAGE_REDUCE] = double(P.n_partials);
+    flops[BISP_STAGE_BIN] = double(P.n_combos) * 4.0 * P.n_lm;
+    return BISP_OK;
+}
+
 const char *estimator_status_string(int status)
 {
     switch (status) {
@@ -529,8 +626,8 @@ int64_t estimator_combo_table(const bisp_plan *p, int64_t cap, int32_t *ints, in
     const HostPlan &P = p->hp;
     const int nr = P.rings.nr;
     for (const Group &G : P.groups)
-        for (int s = 0; s < G.nseg; ++s) {
-            const Segment &q = P.segs[G.seg0 + s];
+        for (int s = 0; s < G.nrow; ++s) {
+            const Row &q = P.rows[G.row0 + s];
             for (int j = 0; j < q.n; ++j) {
                 const int64_t k = G.c0 + q.coff + j;
                 if (k >= cap) continue;

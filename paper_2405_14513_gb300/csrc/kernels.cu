@@ -184,90 +184,155 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
 }
 
 // ---------------------------------------------------------------------------
-// Step II.  One block per item (a group's x chunk).  The block stages the
-// rings of its three planes for TX grid points at a time in shared memory
-// (conjugated for negative planes, D(r,-n) = conj D(r,n)), and each thread
-// takes segments: P = D(r1,n1) D(r2,n2) once per point, then
-// Re(P D(r3+j, n3)) for up to eight r3.  A: per-tile sums; S: block sums.
-template <typename R, typename A, typename S>
-__global__ void __launch_bounds__(256)
-k_step2(StepIIArgs args, const typename Cx<R>::T *__restrict__ dstore)
+// Step II (Eq. fftbs): S(r1, r2, r3) = sum over the M x M grid of
+// D(r1, n1) D(r2, n2) D(r3, n3), for every combination of a plane pair.
+//
+// One block per unit: an x chunk of one group (plane pair and grid) and up
+// to NW of its tiles, one tile per warp.  The block stages the unit's rings
+// of the three planes for TX grid points at a time in shared memory
+// ([slot][x], x contiguous), double-buffered with cp.async.  The lanes of a
+// warp take consecutive grid points, so every shared-memory load is
+// conflict free.  Per point a lane forms the 8 row products
+// P_i = D(r1_i, n1) D(r2_i, n2) once and accumulates Re(P_i D(w0 + j, n3))
+// for the 8 r3 of the tile's window: 64 sums in registers over the whole
+// chunk, reduced across the warp at the end.  Negative planes enter through
+// D(r, -n) = conj D(r, n) as sign factors.  Blocks of 4, 8 and 16 warps
+// (unit classes) let small units share an SM.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
+template <typename R, int NW>
+__global__ void __launch_bounds__(32 * NW, (sizeof(R) == 8 ? 8 : 16) / NW)
+k_step2(StepIIArgs args, int64_t unit0, const typename Cx<R>::T *__restrict__ dstore, int smem_bytes)
 {
     using C = typename Cx<R>::T;
+    constexpr int NT = 32 * NW;
+    constexpr int PER16 = 16 / sizeof(C);     // complex values per 16-byte copy
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Item it = args.items[blockIdx.x];
-    const Group G = args.groups[it.group];
+    const Unit U = args.units[unit0 + blockIdx.x];
+    const Group G = args.groups[U.group];
     const int lg = G.log2m;
     const int64_t M2 = int64_t(1) << (2 * lg);
-    const int64_t x0 = int64_t(it.chunk) * args.x_chunk;
+    const int64_t x0 = int64_t(U.chunk) * args.x_chunk;
     const int64_t x1 = min(M2, x0 + args.x_chunk);
-    const int nr0 = G.rhi[0] - G.rlo[0] + 1, nr1 = G.rhi[1] - G.rlo[1] + 1, nr2 = G.rhi[2] - G.rlo[2] + 1;
-    const int ns = nr0 + nr1 + nr2;
-    const int TX = args.tx, TXP = TX + 1;
+    const int nq0 = U.rhi[0] - U.rlo[0] + 1, nq1 = U.rhi[1] - U.rlo[1] + 1, nq2 = U.rhi[2] - U.rlo[2] + 1;
+    const int ns = nq0 + nq1 + nq2;
 
-    S *acc = reinterpret_cast<S *>(smem_raw);
-    size_t off = (size_t(G.ncombo) * sizeof(S) + 15) & ~size_t(15);
-    int64_t *offs = reinterpret_cast<int64_t *>(smem_raw + off);
-    off += size_t(ns) * sizeof(int64_t);
-    int *cj = reinterpret_cast<int *>(smem_raw + off);
-    off = (off + size_t(ns) * sizeof(int) + 15) & ~size_t(15);
-    C *tile = reinterpret_cast<C *>(smem_raw + off);
+    int64_t *offs = reinterpret_cast<int64_t *>(smem_raw);
+    const size_t off = (size_t(ns) * sizeof(int64_t) + 127) & ~size_t(127);
+    C *buf = reinterpret_cast<C *>(smem_raw + off);
+    // grid points per stage: as many as fit, a multiple of 64, at most 256
+    int TX = int((size_t(smem_bytes) - off) / (2 * size_t(ns) * sizeof(C)));
+    TX = min(256, TX & ~63);
+    const size_t stage_elems = size_t(ns) * TX;
 
-    for (int j = threadIdx.x; j < G.ncombo; j += blockDim.x) acc[j] = S(0);
-    const int nabs[3] = {G.n1 < 0 ? -G.n1 : G.n1, G.n2 < 0 ? -G.n2 : G.n2, G.n3 < 0 ? -G.n3 : G.n3};
-    const int nsg[3] = {G.n1 < 0, G.n2 < 0, G.n3 < 0};
-    for (int s = threadIdx.x; s < ns; s += blockDim.x) {
-        int q = s < nr0 ? 0 : (s < nr0 + nr1 ? 1 : 2);
-        int r = G.rlo[q] + s - (q == 0 ? 0 : (q == 1 ? nr0 : nr0 + nr1));
-        offs[s] = args.doff[(size_t(lg) * args.nz1 + nabs[q]) * kMaxRings + r];
-        cj[s] = nsg[q];
+    for (int s = threadIdx.x; s < ns; s += NT) {
+        const int q = s < nq0 ? 0 : (s < nq0 + nq1 ? 1 : 2);
+        const int r = U.rlo[q] + s - (q == 0 ? 0 : (q == 1 ? nq0 : nq0 + nq1));
+        const int n = q == 0 ? G.n1 : (q == 1 ? G.n2 : G.n3);
+        offs[s] = r < args.nr ? args.doff[(size_t(lg) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
     }
     __syncthreads();
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int64_t xs = x0; xs < x1; xs += TX) {
+    // sign factors of conj(D) for negative planes: with D1 -> (a.x, g1 a.y),
+    // D2 -> (b.x, g2 b.y), D3 -> (c.x, g3 c.y):
+    //   Re(P D3) = Pr c.x - g3 Pi c.y,  Pr = a.x b.x - g1 g2 a.y b.y,
+    //   g3 Pi = g3 g2 a.x b.y + g3 g1 a.y b.x
+    const R g1 = G.n1 < 0 ? R(-1) : R(1), g2 = G.n2 < 0 ? R(-1) : R(1), g3 = G.n3 < 0 ? R(-1) : R(1);
+    const R k12 = -g1 * g2, k32 = g3 * g2, k31 = g3 * g1;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool active = warp < U.nt;
+    Tile T;
+    if (active) T = args.tiles[U.t0 + warp];
+    R a[kTileRows * kTileCols];
+#pragma unroll
+    for (int i = 0; i < kTileRows * kTileCols; ++i) a[i] = R(0);
+
+    const int nstage = int((x1 - x0 + TX - 1) / TX);
+    auto issue = [&](int st) {
+        C *dst = buf + size_t(st & 1) * stage_elems;
+        const int64_t xs = x0 + int64_t(st) * TX;
         const int nx = int(min(int64_t(TX), x1 - xs));
-        for (int s = warp; s < ns; s += nwarp) {
-            const int64_t o = offs[s];
-            const R sg = cj[s] ? R(-1) : R(1);
-            for (int x = lane; x < nx; x += 32) {
-                C v = cmk<C>(0.0, 0.0);
-                if (o >= 0) {   // every staged field is stored; a missing one reads as zero
-                    v = dstore[o + xs + x];
-                    v.y *= sg;
-                }
-                tile[s * TXP + x] = v;
-            }
+        const int per = TX / PER16;                   // 16-byte pieces per slot row
+        for (int k = threadIdx.x; k < ns * per; k += NT) {
+            const int s = k / per, c = (k - s * per) * PER16;
+            C *d = dst + size_t(s) * TX + c;
+            if (offs[s] >= 0 && c < nx) cp_async16(d, dstore + offs[s] + xs + c);
+            else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        asm volatile("cp.async.commit_group;\n" ::);
+    };
+    issue(0);
+    for (int st = 0; st < nstage; ++st) {
+        if (st + 1 < nstage) {
+            issue(st + 1);
+            asm volatile("cp.async.wait_group 1;\n" ::);
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::);
         }
         __syncthreads();
-        for (int g = threadIdx.x; g < G.nseg; g += blockDim.x) {
-            const Segment q = args.segs[G.seg0 + g];
-            const C *t1 = tile + (q.r1 - G.rlo[0]) * TXP;
-            const C *t2 = tile + (nr0 + q.r2 - G.rlo[1]) * TXP;
-            const C *t3 = tile + (nr0 + nr1 + q.r3a - G.rlo[2]) * TXP;
-            const int n = q.n;
-            A p[kSegLen];
+        const C *b = buf + size_t(st & 1) * stage_elems;
+        const int nx = int(min(int64_t(TX), x1 - (x0 + int64_t(st) * TX)));
+        if (active) {
+            // per-stage slot pointers (lane offset included); the x loop
+            // advances them by 64 points and reads two points per lane
+            const int o3 = T.s3 * TX + lane;
+            int o1[kTileRows], o2[kTileRows];
 #pragma unroll
-            for (int j = 0; j < kSegLen; ++j) p[j] = A(0);
-            for (int x = 0; x < nx; ++x) {
-                const C u = t1[x], v = t2[x];
-                const A pr = A(u.x) * A(v.x) - A(u.y) * A(v.y);
-                const A pi = A(u.x) * A(v.y) + A(u.y) * A(v.x);
-#pragma unroll
-                for (int j = 0; j < kSegLen; ++j)
-                    if (j < n) {
-                        const C w = t3[j * TXP + x];
-                        p[j] += pr * A(w.x) - pi * A(w.y);
-                    }
+            for (int i = 0; i < kTileRows; ++i) {
+                o1[i] = T.s1[i] * TX + lane;
+                o2[i] = T.s2[i] * TX + lane;
             }
+            for (int xc = 0; xc < nx; xc += 64) {
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    const int x = xc + 32 * h;
+                    C w[kTileCols];
 #pragma unroll
-            for (int j = 0; j < kSegLen; ++j)
-                if (j < n) acc[q.coff + j] += S(p[j]);
+                    for (int j = 0; j < kTileCols; ++j) w[j] = b[o3 + j * TX + x];
+#pragma unroll
+                    for (int i = 0; i < kTileRows; ++i) {
+                        const C u = b[o1[i] + x];
+                        const C v = b[o2[i] + x];
+                        const R pr = fma(u.x, v.x, k12 * (u.y * v.y));
+                        const R npi = -fma(k32 * u.x, v.y, k31 * (u.y * v.x));
+#pragma unroll
+                        for (int j = 0; j < kTileCols; ++j) {
+                            R &acc = a[i * kTileCols + j];
+                            acc = fma(pr, w[j].x, acc);
+                            acc = fma(npi, w[j].y, acc);
+                        }
+                    }
+                }
+            }
         }
         __syncthreads();
     }
-    double *dst = args.partials + G.part0 + int64_t(it.chunk) * G.ncombo;
-    for (int j = threadIdx.x; j < G.ncombo; j += blockDim.x) dst[j] = double(acc[j]);
+    if (!active) return;
+    // butterfly reduction across the warp: after the step with offset o the
+    // lane keeps the half of its sums selected by (lane & o); at the end lane
+    // l holds the sums of tile entries 2 l and 2 l + 1
+#pragma unroll
+    for (int o = 16, n = kTileRows * kTileCols / 2; o >= 1; o >>= 1, n >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int k = 0; k < kTileRows * kTileCols / 2; ++k) {
+            if (k >= n) break;
+            const R keep = up ? a[k + n] : a[k];
+            const R give = up ? a[k] : a[k + n];
+            a[k] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+        }
+    }
+    double *dst = args.partials + G.part0 + int64_t(U.chunk) * G.ncombo;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int idx = 2 * lane + k;
+        if ((T.mask[idx >> 5] >> (idx & 31)) & 1u) dst[T.coff[idx / kTileCols] + (idx % kTileCols)] = double(a[k]);
+    }
 }
 
 template <typename A>
@@ -289,19 +354,19 @@ k_reduce(const Group *__restrict__ groups, const double *__restrict__ partials, 
 __constant__ double c_nlm[9][9];
 __constant__ double c_pref[9];
 
-template <typename W>
+template <typename W, int LMAX>
 __global__ void __launch_bounds__(256)
 k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ bin_start, int64_t nbins,
-           const double *__restrict__ value, int l_max, const double *__restrict__ den, double norm,
+           const double *__restrict__ value, const double *__restrict__ den, double norm,
            double *__restrict__ out)
 {
-    constexpr int kMaxLm = 25;
+    constexpr int NLM = (LMAX / 2 + 1) * (LMAX / 2 + 1);
     const int64_t b = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nbins) return;   // whole warps leave together
-    W acc[kMaxLm];
+    W acc[NLM];
 #pragma unroll
-    for (int i = 0; i < kMaxLm; ++i) acc[i] = W(0);
+    for (int i = 0; i < NLM; ++i) acc[i] = W(0);
     const int64_t k0 = bin_start[b], k1 = bin_start[b + 1];
     for (int64_t k = k0 + lane; k < k1; k += 32) {
         const Record R = rec[k];
@@ -311,14 +376,16 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
         const bool deg = (R.flags & 2) != 0;
         const W s = sqrt(max(W(0), W(1) - x * x));
         W pmm = W(1), tm1 = W(1), tm2 = W(1);   // P_m^m; cos(m phi), cos((m-1) phi)
-        for (int m = 0; m <= l_max; ++m) {
+#pragma unroll
+        for (int m = 0; m <= LMAX; ++m) {
             W tm;
             if (m == 0) tm = W(1);
             else if (m == 1) tm = c;
             else tm = W(2) * c * tm1 - tm2;
             if (m > 0) pmm *= -W(2 * m - 1) * s;
             W plm1 = W(0), pl = pmm;                 // P_{l-1}^m, P_l^m at l = m
-            for (int l = m; l <= l_max; ++l) {
+#pragma unroll
+            for (int l = m; l <= LMAX; ++l) {
                 if ((l & 1) == 0) {
                     const W y = W(c_nlm[l][m]) * pl;
                     const int idx = (l >> 1) * (l >> 1) + m;
@@ -337,18 +404,18 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
             tm1 = tm;
         }
     }
-    const int nlm = (l_max / 2 + 1) * (l_max / 2 + 1);
-    for (int i = 0; i < nlm; ++i) {
+#pragma unroll
+    for (int i = 0; i < NLM; ++i) {
         W v = acc[i];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if (lane == 0) {
             if (mode == 0) {
                 int l = 0;
                 while ((l / 2 + 1) * (l / 2 + 1) <= i) l += 2;
-                const double d = den[b * nlm + i];
-                out[b * nlm + i] = d > 0.0 ? c_pref[l] * double(v) * norm / d : __longlong_as_double(0x7ff8000000000000LL);
+                const double d = den[b * NLM + i];
+                out[b * NLM + i] = d > 0.0 ? c_pref[l] * double(v) * norm / d : __longlong_as_double(0x7ff8000000000000LL);
             } else {
-                out[b * nlm + i] = double(v);
+                out[b * NLM + i] = double(v);
             }
         }
     }
@@ -463,15 +530,32 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     return cudaGetLastError();
 }
 
-template <typename R, typename A, typename S>
-cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t nitems, size_t smem,
+template <typename R, int NW>
+cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t u0, int64_t n,
+                               size_t smem, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    cudaError_t e = set_smem(k_step2<R, NW>, smem);
+    if (e != cudaSuccess) return e;
+    k_step2<R, NW><<<unsigned(n), 32 * NW, smem, s>>>(a, u0, dstore, int(smem));
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
                          cudaStream_t s)
 {
-    if (nitems == 0) return cudaSuccess;
-    cudaError_t e = set_smem(k_step2<R, A, S>, smem);
-    if (e != cudaSuccess) return e;
-    k_step2<R, A, S><<<unsigned(nitems), 256, smem, s>>>(a, dstore);
-    return cudaGetLastError();
+    cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
+                                             kStep2ClassSmem[2], s);
+    if (e == cudaSuccess)
+        e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
+                                     kStep2ClassSmem[3], s);
+    if constexpr (sizeof(R) == 4) {   // FP64 blocks have at most 8 warps (register file)
+        if (e == cudaSuccess)
+            e = launch_step2_class<R, 16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
+                                          kStep2ClassSmem[4], s);
+    }
+    return e;
 }
 
 template <typename A>
@@ -489,8 +573,15 @@ cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_star
                             cudaStream_t s)
 {
     if (nbins == 0) return cudaSuccess;
-    const int64_t nblk = (nbins * 32 + 255) / 256;
-    k_epilogue<W><<<unsigned(nblk), 256, 0, s>>>(mode, rec, bin_start, nbins, value, l_max, den, norm, out);
+    const unsigned nblk = unsigned((nbins * 32 + 255) / 256);
+    switch (l_max) {
+    case 0: k_epilogue<W, 0><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    case 2: k_epilogue<W, 2><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    case 4: k_epilogue<W, 4><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    case 6: k_epilogue<W, 6><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    case 8: k_epilogue<W, 8><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -516,9 +607,8 @@ template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int
 template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const double2 *, int, cudaStream_t);
 template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const float2 *, int, cudaStream_t);
 template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const double2 *, int, cudaStream_t);
-template cudaError_t launch_step2<float, float, float>(const StepIIArgs &, const float2 *, int64_t, size_t, cudaStream_t);
-template cudaError_t launch_step2<float, float, double>(const StepIIArgs &, const float2 *, int64_t, size_t, cudaStream_t);
-template cudaError_t launch_step2<double, double, double>(const StepIIArgs &, const double2 *, int64_t, size_t, cudaStream_t);
+template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, cudaStream_t);
+template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
 template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
 template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, cudaStream_t);

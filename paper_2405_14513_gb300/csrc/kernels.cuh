@@ -29,12 +29,12 @@ struct Job {
 
 struct StepIIArgs {
     const Group *groups;
-    const Segment *segs;
-    const Item *items;
+    const Tile *tiles;
+    const Unit *units;
     const int64_t *doff;     // [kMaxLevels][nz+1][kMaxRings]
-    int nz1;
-    int64_t x_chunk;
-    int tx;                  // x points per shared-memory tile
+    int nz1;                 // planes stored: 0 .. nz1 - 1
+    int nr;                  // rings per plane
+    int64_t x_chunk;         // grid points of one unit
     double *partials;
 };
 
@@ -63,11 +63,12 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
                                typename Cx<R>::T *gt, const typename Cx<R>::T *tw, int lg_tw,
                                cudaStream_t s);
 
-// Step II: partial triple sums of every item (A: sums over one shared-memory
-// tile, S: block sums over the item's chunk).
-template <typename R, typename A, typename S>
-cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t nitems,
-                         size_t smem, cudaStream_t s);
+// Step II: partial triple sums of every unit, one block per unit, one launch
+// per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
+// 2^c warps with kStep2ClassSmem[c] bytes of shared memory).
+template <typename R>
+cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
+                         cudaStream_t s);
 
 // S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
 template <typename A>

@@ -184,17 +184,23 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     // used[l][n][r]: D fields to store
     const int lgmax = [&] { int l = 0; while ((1 << l) < R.ng) ++l; return l; }();
     std::vector<uint8_t> used(size_t(kMaxLevels) * (nz + 1) * kMaxRings, 0);
-    auto U = [&](int lg, int n, int r) -> uint8_t & {
+    auto U_ = [&](int lg, int n, int r) -> uint8_t & {
         return used[(size_t(lg) * (nz + 1) + n) * kMaxRings + r];
     };
 
     P.groups.clear();
-    P.segs.clear();
+    P.rows.clear();
+    P.tiles.clear();
+    P.units.clear();
     P.records_s.clear();
     P.ntri_s.clear();
     P.n_combos = 0;
     P.n_pairs = 0;
     P.triple_products = 0;
+    P.pair_products = 0;
+    P.max_slots = 0;
+    std::vector<Unit> unit_tmpl;                 // per group: tile ranges and staged rings
+    std::vector<int32_t> group_unit0(1, 0);      // first template of each group
     int64_t cidx = 0;
     for (size_t k = 0; k < outs.size(); ++k) {
         PairOut &po = outs[k];
@@ -205,11 +211,12 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             Group G{};
             G.n1 = n1; G.n2 = n2; G.n3 = n3;
             G.log2m = lg;
-            G.seg0 = int32_t(P.segs.size());
+            G.row0 = int32_t(P.rows.size());
             G.c0 = cidx;
             G.self_conj = (n1 == 0 && n2 == 0) ? 1 : 0;
-            for (int q = 0; q < 3; ++q) { G.rlo[q] = nr; G.rhi[q] = -1; }
             int ncombo = 0;
+            int64_t nrowpair = 0;
+            int last_r1 = -1, last_r2 = -1;
             size_t i = 0;
             while (i < po.acc.size()) {
                 if (po.acc[i].lg != lg) { ++i; continue; }
@@ -218,15 +225,16 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                 size_t j = i + 1;
                 int r3 = a.r3;
                 while (j < po.acc.size() && po.acc[j].lg == lg && po.acc[j].r1 == a.r1 &&
-                       po.acc[j].r2 == a.r2 && po.acc[j].r3 == r3 + 1 && (j - i) < size_t(kSegLen)) {
+                       po.acc[j].r2 == a.r2 && po.acc[j].r3 == r3 + 1 && (j - i) < size_t(255)) {
                     ++j;
                     ++r3;
                 }
-                Segment s{a.r1, a.r2, a.r3, uint8_t(j - i), ncombo};
-                P.segs.push_back(s);
-                G.rlo[0] = std::min<int>(G.rlo[0], a.r1); G.rhi[0] = std::max<int>(G.rhi[0], a.r1);
-                G.rlo[1] = std::min<int>(G.rlo[1], a.r2); G.rhi[1] = std::max<int>(G.rhi[1], a.r2);
-                G.rlo[2] = std::min<int>(G.rlo[2], a.r3); G.rhi[2] = std::max<int>(G.rhi[2], r3);
+                P.rows.push_back(Row{a.r1, a.r2, a.r3, uint8_t(j - i), ncombo});
+                if (a.r1 != last_r1 || a.r2 != last_r2) {
+                    ++nrowpair;
+                    last_r1 = a.r1;
+                    last_r2 = a.r2;
+                }
                 for (size_t q = i; q < j; ++q) {
                     const Acc &c = po.acc[q];
                     Record rec;
@@ -238,21 +246,104 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                     P.ntri_s.push_back(double(P.ntri[(size_t(c.r1) * nr + c.r2) * nr + c.r3]));
                     ++ncombo;
                 }
-                // skip the run (later entries of other grids stay)
-                for (size_t q = i; q < j; ++q) po.acc[q].lg = 255;
                 i = j;
             }
             if (ncombo == 0) continue;
-            G.nseg = int32_t(P.segs.size()) - G.seg0;
+            G.nrow = int32_t(P.rows.size()) - G.row0;
             G.ncombo = ncombo;
             const int64_t M2 = int64_t(1) << (2 * lg);
             G.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
             P.triple_products += double(ncombo) * double(M2);
+            P.pair_products += double(nrowpair) * double(M2);
             cidx += ncombo;
-            const int ns[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
-            for (int q = 0; q < 3; ++q)
-                for (int r = G.rlo[q]; r <= G.rhi[q]; ++r) U(lg, ns[q], r) = 1;
+
+            // register tiles: rows ordered by the centre of their r3 run,
+            // blocks of kTileRows rows, each block cut into windows of
+            // kTileCols consecutive r3 covering the union of its runs
+            std::vector<int> order(G.nrow);
+            for (int q = 0; q < G.nrow; ++q) order[q] = q;
+            const Row *rw = P.rows.data() + G.row0;
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                int cx = 2 * rw[x].r3a + rw[x].n, cy = 2 * rw[y].r3a + rw[y].n;
+                return cx != cy ? cx < cy : rw[x].r3a < rw[y].r3a;
+            });
+            struct Raw { int rows[kTileRows]; int nr; int w0; };
+            std::vector<Raw> raws;
+            for (int b = 0; b < G.nrow; b += kTileRows) {
+                Raw base{};
+                base.nr = std::min(kTileRows, G.nrow - b);
+                for (int q = 0; q < base.nr; ++q) base.rows[q] = order[b + q];
+                std::vector<uint8_t> cov(kMaxRings + kTileCols, 0);
+                for (int q = 0; q < base.nr; ++q)
+                    for (int c = 0; c < rw[base.rows[q]].n; ++c) cov[rw[base.rows[q]].r3a + c] = 1;
+                for (int c = 0; c < kMaxRings; ++c) {
+                    if (!cov[c]) continue;
+                    Raw t = base;
+                    t.w0 = c;
+                    raws.push_back(t);
+                    for (int d = 0; d < kTileCols; ++d) cov[c + d] = 0;
+                }
+            }
+            // units: runs of 16, 8 or 4 consecutive tiles (one per warp), each
+            // staging the union of its tiles' rings
+            size_t u0 = 0;
+            while (u0 < raws.size()) {
+                const size_t rem = raws.size() - u0;
+                int cls = rem >= 16 ? 4 : (rem >= 8 ? 3 : 2);
+                if (cls > P.max_cls) cls = P.max_cls;
+                const size_t take = std::min(rem, size_t(1) << cls);
+                const size_t u1 = u0 + take;
+                Unit U{};
+                U.t0 = int32_t(P.tiles.size());
+                U.nt = int32_t(take);
+                int lo[3] = {nr, nr, kMaxRings}, hi[3] = {-1, -1, -1};
+                for (size_t t = u0; t < u1; ++t) {
+                    const Raw &w = raws[t];
+                    for (int q = 0; q < w.nr; ++q) {
+                        const Row &r = rw[w.rows[q]];
+                        lo[0] = std::min<int>(lo[0], r.r1); hi[0] = std::max<int>(hi[0], r.r1);
+                        lo[1] = std::min<int>(lo[1], r.r2); hi[1] = std::max<int>(hi[1], r.r2);
+                    }
+                    lo[2] = std::min(lo[2], w.w0);
+                    hi[2] = std::max(hi[2], w.w0 + kTileCols - 1);
+                }
+                for (int q = 0; q < 3; ++q) { U.rlo[q] = int16_t(lo[q]); U.rhi[q] = int16_t(hi[q]); }
+                const int nq0 = hi[0] - lo[0] + 1, nq1 = hi[1] - lo[1] + 1, nq2 = hi[2] - lo[2] + 1;
+                const int ns = nq0 + nq1 + nq2;
+                if (ns > 255) return "too many staged rings in a Step-II unit";
+                // a class whose shared memory holds two stages of 64 points
+                while (cls < P.max_cls && step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls]) ++cls;
+                if (step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls])
+                    return "Step-II unit too large for shared memory";
+                U.cls = cls;
+                P.max_slots = std::max(P.max_slots, ns);
+                for (size_t t = u0; t < u1; ++t) {
+                    const Raw &w = raws[t];
+                    Tile T{};
+                    for (int q = 0; q < kTileRows; ++q) {
+                        const Row &r = rw[w.rows[q < w.nr ? q : 0]];
+                        T.s1[q] = uint8_t(r.r1 - lo[0]);
+                        T.s2[q] = uint8_t(nq0 + r.r2 - lo[1]);
+                        T.coff[q] = r.coff + (w.w0 - r.r3a);
+                        if (q >= w.nr) continue;
+                        for (int d = 0; d < kTileCols; ++d) {
+                            const int r3 = w.w0 + d;
+                            if (r3 >= r.r3a && r3 < r.r3a + r.n)
+                                T.mask[(q * kTileCols + d) >> 5] |= 1u << ((q * kTileCols + d) & 31);
+                        }
+                    }
+                    T.s3 = uint8_t(nq0 + nq1 + w.w0 - lo[2]);
+                    P.tiles.push_back(T);
+                }
+                const int nsabs[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
+                for (int q = 0; q < 3; ++q)
+                    for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lg, nsabs[q], r) = 1;
+                U.group = int32_t(P.groups.size());
+                unit_tmpl.push_back(U);
+                u0 = u1;
+            }
             P.groups.push_back(G);
+            group_unit0.push_back(int32_t(unit_tmpl.size()));
         }
         std::vector<Acc>().swap(po.acc);
     }
@@ -271,7 +362,7 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
         const int64_t M2 = int64_t(1) << (2 * lg);
         for (int n = 0; n <= nz; ++n)
             for (int r = 0; r < nr; ++r)
-                if (U(lg, n, r)) {
+                if (U_(lg, n, r)) {
                     P.doff[(size_t(lg) * (nz + 1) + n) * kMaxRings + r] = cursor;
                     cursor += M2;
                     L.njobs++;
@@ -283,24 +374,44 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     }
     P.dstore_elems = cursor;
 
-    // partial-sum layout and Step-II items: biggest grids first, then by
-    // chunk, then in pair order, so that concurrent blocks share planes
+    // partial-sum layout and Step-II units in launch order: biggest grids
+    // first, then by x chunk, then by blocks of 8 x 8 plane pairs, so that
+    // blocks running together share planes (and their rings) in L2
     int64_t part = 0;
     for (auto &G : P.groups) {
         G.part0 = part;
         part += int64_t(G.nchunk) * G.ncombo;
     }
     P.n_partials = part;
-    P.items.clear();
-    for (int lg = lgmax; lg >= kMinLog2M; --lg) {
-        int maxchunk = 0;
-        for (auto &G : P.groups)
-            if (G.log2m == lg) maxchunk = std::max(maxchunk, G.nchunk);
-        for (int c = 0; c < maxchunk; ++c)
-            for (size_t g = 0; g < P.groups.size(); ++g)
-                if (P.groups[g].log2m == lg && c < P.groups[g].nchunk)
-                    P.items.push_back(Item{int32_t(g), int32_t(c)});
+    std::vector<int32_t> gorder(P.groups.size());
+    for (size_t g = 0; g < gorder.size(); ++g) gorder[g] = int32_t(g);
+    auto blk = [&](const Group &G) { return std::make_pair((G.n1) / 8, (G.n2 + nz) / 8); };
+    std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) {
+        const Group &A = P.groups[a], &B = P.groups[b];
+        if (A.log2m != B.log2m) return A.log2m > B.log2m;
+        return blk(A) < blk(B);
+    });
+    // units grouped by block class; within a class: grid, x chunk, pair block
+    for (int cls = 2; cls <= 4; ++cls) {
+        P.class_begin[cls] = int64_t(P.units.size());
+        for (int lg = lgmax; lg >= kMinLog2M; --lg) {
+            int maxchunk = 0;
+            for (auto &G : P.groups)
+                if (G.log2m == lg) maxchunk = std::max(maxchunk, G.nchunk);
+            for (int c = 0; c < maxchunk; ++c)
+                for (int32_t g : gorder) {
+                    const Group &G = P.groups[g];
+                    if (G.log2m != lg || c >= G.nchunk) continue;
+                    for (int32_t u = group_unit0[g]; u < group_unit0[g + 1]; ++u) {
+                        if (unit_tmpl[u].cls != cls) continue;
+                        Unit U = unit_tmpl[u];
+                        U.chunk = c;
+                        P.units.push_back(U);
+                    }
+                }
+        }
     }
+    P.class_begin[5] = int64_t(P.units.size());
     return "";
 }
 
@@ -311,12 +422,12 @@ void sort_records(HostPlan &P)
     std::vector<int32_t> bin(P.records_s.size());
     const Rings &R = P.rings;
     for (const auto &G : P.groups)
-        for (int s = 0; s < G.nseg; ++s) {
-            const Segment &sg = P.segs[G.seg0 + s];
-            for (int j = 0; j < sg.n; ++j) {
+        for (int s = 0; s < G.nrow; ++s) {
+            const Row &rw = P.rows[G.row0 + s];
+            for (int j = 0; j < rw.n; ++j) {
                 Geo g;
-                combo_geometry(P, R.kperp[sg.r1], R.kperp[sg.r2], R.kperp[sg.r3a + j], G.n1, G.n2, G.n3, &g);
-                bin[G.c0 + sg.coff + j] = g.bin;
+                combo_geometry(P, R.kperp[rw.r1], R.kperp[rw.r2], R.kperp[rw.r3a + j], G.n1, G.n2, G.n3, &g);
+                bin[G.c0 + rw.coff + j] = g.bin;
             }
         }
     P.combo_bin = bin;

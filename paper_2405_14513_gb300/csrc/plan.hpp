@@ -14,7 +14,8 @@ namespace bisp {
 constexpr int kMaxRings = 64;     // N_r for N_g <= 1024 is 52
 constexpr int kMaxLevels = 11;    // reduction grids M = 2^3 .. 2^10
 constexpr int kMinLog2M = 3;      // smallest reduction grid, 8 x 8
-constexpr int kSegLen = 8;        // r3 values per Step-II segment
+constexpr int kTileRows = 8;      // rows (r1, r2) of a Step-II register tile
+constexpr int kTileCols = 8;      // consecutive r3 of a Step-II register tile
 
 // Ring table (Sec. II, implementation paragraph): ring r holds the modes
 // u = (i, j) with e_{r} <= |u| < e_{r+1}; e_0 = 0, widths 2^floor(r/10)
@@ -30,32 +31,62 @@ struct Rings {
 };
 
 // Plane pair (n1, n2, n3 = -n1 - n2) on one reduction grid M: the set of
-// ring triples whose triple sum runs on the M x M grid.
+// ring triples whose triple sum runs on the M x M grid.  Its combinations
+// are ordered by (r1, r2, r3).
 struct Group {
     int32_t n1, n2, n3;        // signed planes
     int32_t log2m;             // reduction grid M = 2^log2m
-    int32_t seg0, nseg;        // segments of this group
+    int32_t row0, nrow;        // rows of this group
     int64_t c0;                // index of the first combination (S order)
     int32_t ncombo;
     int32_t nchunk;            // x chunks of the M^2 grid
-    int32_t rlo[3], rhi[3];    // ring ranges staged for planes 1, 2, 3
     int32_t self_conj;         // 1 for n1 = n2 = 0 (counted once), else 0
+    int32_t pad;
     int64_t part0;             // partial sums [nchunk][ncombo] start here
 };
 
-// A run of up to kSegLen combinations (r1, r2, r3a + j), j < n, sharing the
-// product D(r1, n1) D(r2, n2).  coff is the offset of the run's first
-// combination inside its group.
-struct Segment {
+// A run of consecutive r3 (r3a .. r3a + n - 1) accepted for (r1, r2): the
+// combinations coff .. coff + n - 1 of its group.
+struct Row {
     uint8_t r1, r2, r3a, n;
     int32_t coff;
 };
 
-// One Step-II launch unit: a chunk of the x grid of a group.
-struct Item {
-    int32_t group;
-    int32_t chunk;
+// Step-II register tile: up to 8 rows (r1, r2) of one group times 8
+// consecutive r3 (the window w0 .. w0 + 7).  Slots index the rings staged
+// by the tile's unit in shared memory.
+struct Tile {
+    uint8_t s1[kTileRows];     // slot of D(r1, n1) of each row
+    uint8_t s2[kTileRows];     // slot of D(r2, n2) of each row
+    uint8_t s3;                // slot of D(w0, n3); the window is s3 .. s3 + 7
+    uint8_t pad[3];
+    uint32_t mask[2];          // bit 8 i + j: (row i, r3 = w0 + j) is a combination
+    int32_t coff[kTileRows];   // combination (in the group) of (row i, w0); (i, j) -> coff[i] + j
+    int32_t pad2;
 };
+static_assert(sizeof(Tile) == 64, "Tile is copied in 16-byte pieces");
+
+// One Step-II block: an x chunk of a group with up to 16 of its tiles (one
+// per warp), and the ring ranges it stages per plane (plane 3 may reach
+// past the last ring; those slots are zero).  cls: log2 of the warps of the
+// block class it runs in (2, 3 or 4).
+struct Unit {
+    int32_t group, chunk;
+    int32_t t0, nt;
+    int16_t rlo[3], rhi[3];
+    int32_t cls;
+};
+
+// Shared-memory bytes of a Step-II block staging ns rings, two stages of tx
+// grid points of celem-byte values.
+inline size_t step2_smem_need(int ns, int tx, size_t celem)
+{
+    return ((size_t(ns) * sizeof(int64_t) + 127) & ~size_t(127)) + 2 * size_t(ns) * size_t(tx) * celem;
+}
+
+// Dynamic shared memory of a block of each class (2, 3, 4 = 4, 8, 16 warps):
+// 1, 2 or 4 blocks share the 227 KB of an SM.
+constexpr size_t kStep2ClassSmem[5] = {0, 0, 55 * 1024, 111 * 1024, 222 * 1024};
 
 // Per-combination data of the binning epilogue, in (k1, mu, t)-bin order.
 struct Record {
@@ -86,16 +117,19 @@ struct HostPlan {
 
     // combinations in S order
     std::vector<Group> groups;
-    std::vector<Segment> segs;
-    std::vector<Item> items;
+    std::vector<Row> rows;
+    std::vector<Tile> tiles;
+    std::vector<Unit> units;            // Step-II blocks in launch order
+    int max_slots = 0;                  // largest staged ring count of a unit
+    int max_cls = 4;                    // largest block class (set before enumerate)
+    size_t celem = 8;                   // bytes of a staged complex value (set before enumerate)
+    int64_t class_begin[6] = {};        // units of class c: [class_begin[c], class_begin[c+1])
     int64_t n_combos = 0;
     int64_t n_partials = 0;
     int64_t n_pairs = 0;
-    double triple_products = 0;
-    std::vector<int32_t> combo_ints;    // [n_combos][6]  n1 n2 n3 r1 r2 r3
-    std::vector<int64_t> combo_ntri;
-    std::vector<int32_t> combo_bin;
-    std::vector<int32_t> combo_grid;
+    double triple_products = 0;          // sum over combinations of M^2
+    double pair_products = 0;            // sum over distinct (group, r1, r2) of M^2
+    std::vector<int32_t> combo_bin;      // S order
     std::vector<Record> records_s;      // S order (moved to bin order later)
     std::vector<double> ntri_s;         // N_tri per combination, S order
 
@@ -122,8 +156,8 @@ bool build_rings(int ng, Rings &R);
 int triple_log2m(const Rings &R, int r1, int r2, int r3);
 
 // Enumerate the accepted combinations of one half of the plane pairs and
-// fill groups, segments, items, records, combination tables and the D-store
-// layout.  Requires rings and ntri.  Returns "" or an error message.
+// fill groups, rows, tiles, units, records and the D-store layout.
+// Requires rings and ntri.  Returns "" or an error message.
 std::string enumerate(HostPlan &P, int64_t x_chunk);
 
 // Counting sort of the records by (k1, mu, t) bin.

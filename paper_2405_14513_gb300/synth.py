@@ -24,6 +24,8 @@ f_NG = 0.5, beta = 0.5.  The paper's own run used beta = 1 (Sec. III.B).
 """
 from __future__ import annotations
 
+import math
+
 import numpy as np
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -102,3 +104,68 @@ def default_k1_edges(ng: int, box_len: float, n_k1: int) -> np.ndarray:
     e = np.linspace(ng / 12.0, ng / 3.0, n_k1 + 1) * kf
     e[-1] = (ng / 3.0) * kf
     return e
+
+
+# ---------------------------------------------------------------------------
+# The same recipe with torch (for large grids on a GPU): the noise stream is
+# bit-identical to white_noise(); the transforms run in float64 with torch.fft.
+def _splitmix64_torch(x):
+    import torch
+
+    def srl(v, k):   # logical right shift of int64 bit patterns
+        return torch.bitwise_and(torch.bitwise_right_shift(v, k), (1 << (64 - k)) - 1)
+
+    g = 0x9E3779B97F4A7C15 - (1 << 64)
+    m1 = 0xBF58476D1CE4E5B9 - (1 << 64)
+    m2 = 0x94D049BB133111EB - (1 << 64)
+    z = x + g
+    z = torch.bitwise_xor(z, srl(z, 30)) * m1
+    z = torch.bitwise_xor(z, srl(z, 27)) * m2
+    return torch.bitwise_xor(z, srl(z, 31))
+
+
+def white_noise_torch(n: int, seed: int, device="cpu", chunk: int = 1 << 24):
+    import torch
+    out = torch.empty(n, dtype=torch.float64, device=device)
+    base = seed * 0x100000000
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        i = torch.arange(s, e, dtype=torch.int64, device=device)
+        a = _splitmix64_torch(base + 2 * i)
+        b = _splitmix64_torch(base + 2 * i + 1)
+        ua = torch.bitwise_and(torch.bitwise_right_shift(a, 11), (1 << 53) - 1).to(torch.float64)
+        ub = torch.bitwise_and(torch.bitwise_right_shift(b, 11), (1 << 53) - 1).to(torch.float64)
+        u1 = (ua + 1.0) * (1.0 / 9007199254740992.0)
+        u2 = ub * (1.0 / 9007199254740992.0)
+        out[s:e] = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+    return out
+
+
+def make_field_torch(ng: int, box_len: float, seed: int, device="cpu", sigma_g: float = 0.1,
+                     f_ng: float = 0.5, beta: float = 0.5, index: float = -2.0):
+    """make_field() computed with torch on `device`; float64 [ng][ng][ng]."""
+    import torch
+    V = box_len ** 3
+    w = white_noise_torch(ng ** 3, seed, device).reshape(ng, ng, ng)
+    W = torch.fft.rfftn(w)
+    del w
+    kf = 2.0 * math.pi / box_len
+    k1 = torch.fft.fftfreq(ng, d=1.0 / ng, dtype=torch.float64, device=device) * kf
+    kz = torch.fft.rfftfreq(ng, d=1.0 / ng, dtype=torch.float64, device=device) * kf
+    k = torch.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + kz[None, None, :] ** 2)
+    kfull = torch.sqrt(k1[:, None, None] ** 2 + k1[None, :, None] ** 2 + k1[None, None, :] ** 2)
+    kfull = kfull.reshape(-1)[1:]
+    A = float(sigma_g ** 2 * V / torch.sum(kfull ** index))
+    del kfull
+    kk = torch.where(k > 0, k, torch.ones_like(k))
+    amp = torch.sqrt(A * kk ** index * ng ** 3 / V)
+    amp[0, 0, 0] = 0.0
+    dG = torch.fft.irfftn(W * amp, s=(ng, ng, ng), dim=(0, 1, 2))
+    del W, amp
+    d = dG + f_ng * (dG * dG - torch.mean(dG * dG))
+    del dG
+    D = torch.fft.rfftn(d)
+    del d
+    mu2 = torch.where(k > 0, (kz[None, None, :] / kk) ** 2, torch.zeros_like(k))
+    D *= 1.0 + beta * mu2
+    return torch.fft.irfftn(D, s=(ng, ng, ng), dim=(0, 1, 2))
