@@ -134,6 +134,30 @@ const char *estimator_status_string(int status);
 /* Description of the last failure on the calling thread ("" if none). */
 const char *estimator_last_error(void);
 
+/* ---------------- estimate without caller-provided workspace ---------------- */
+
+/* estimator_estimate for callers that cannot allocate device memory: code
+ * running while a stream is captured into a CUDA graph, code under a memory
+ * manager that owns the device heap, plugins given a device and a stream but
+ * no allocator.  (The paper has no counterpart: this is a deployment entry
+ * point.)
+ *   delta, batch, B, stream: as for estimator_estimate (DEVICE pointers);
+ *   the workspace is a file-scope device array of the library,
+ *   estimator_static_scratch_bytes() = 64 MiB, held on every GPU where the
+ *   library is loaded until the process exits.
+ * Allocates nothing.  Returns BISP_INVALID_ARG (see estimator_last_error)
+ * when the plan's workspace for `batch` fields is larger than the array.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (on any
+ * streams, with any plans) race and give wrong results; serialise them.
+ * Stage timing (estimator_set_timing) must be off for the call to allocate
+ * nothing (timing creates CUDA events). */
+int estimator_estimate_static(bisp_plan *plan, const void *delta, int batch, double *B, void *stream);
+
+/* Bytes of the device array used by estimator_estimate_static. */
+size_t estimator_static_scratch_bytes(void);
+
 /* ---------------- stage timing ---------------- */
 
 /* Stages timed by estimator_stage_times. */

@@ -48,6 +48,12 @@ int ilog2i(int v)
 
 }  // namespace
 
+namespace bisp {
+// Record a failure message for estimator_last_error() from another
+// translation unit of the library.
+int record_error(int code, const char *msg) { return fail(code, msg); }
+}  // namespace bisp
+
 struct bisp_plan {
     HostPlan hp;
     int precision = BISP_PREC_MIXED;

@@ -1,0 +1,74 @@
+"""estimator_estimate_static: the estimate for callers that cannot allocate
+device memory (stream capture, a memory manager that owns the heap, plugins
+without an allocator) keeps its workspace in a static device array of the
+library.  Its results must equal those of estimator_estimate with a caller
+workspace, on repeated calls (the array keeps the previous call's contents),
+and plans too large for the array must be refused with a clear error.
+
+This file is collected last on purpose: the first call of the entry point
+on a device loads the array, and the test must pass both on its own in a
+fresh process and after every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2405_14513_gb300 import api, synth  # noqa: E402
+
+TOL = 1e-4   # the FP32-transform tolerance of the GPU parity tests
+
+
+def _lib():
+    lib = api.load()
+    lib.estimator_estimate_static.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+    lib.estimator_estimate_static.restype = C.c_int
+    lib.estimator_static_scratch_bytes.argtypes = []
+    lib.estimator_static_scratch_bytes.restype = C.c_size_t
+    return lib
+
+
+def _floored_rel_err(got, ref):
+    fin = np.isfinite(ref)
+    assert np.array_equal(fin, np.isfinite(got)), "empty-bin pattern differs"
+    g = np.where(fin, got, 0.0).reshape(-1, ref.shape[-1])
+    r = np.where(fin, ref, 0.0).reshape(-1, ref.shape[-1])
+    floor = 1e-2 * np.abs(r).max(axis=0, keepdims=True)
+    return (np.abs(g - r) / np.maximum(np.abs(r), np.maximum(floor, 1e-300))).max()
+
+
+def test_static_scratch_matches_caller_workspace():
+    lib = _lib()
+    ng, L = 64, 1000.0
+    plan = api.Plan(ng, L, synth.default_k1_edges(ng, L, 6), 5, 5, 6, precision="mixed")
+    assert 0 < plan.workspace_bytes(1) <= lib.estimator_static_scratch_bytes()
+    field = torch.from_numpy(synth.make_field(ng, L, 3).astype(np.float32)).cuda()[None].contiguous()
+    ref = plan.estimate(field, plan.workspace(1)).cpu().numpy()
+    stream = torch.cuda.current_stream()
+    for call in range(2):
+        out = torch.full(plan.out_shape(1), float("nan"), dtype=torch.float64, device="cuda")
+        st = lib.estimator_estimate_static(plan._h, C.c_void_p(field.data_ptr()), 1,
+                                           C.c_void_p(out.data_ptr()), C.c_void_p(stream.cuda_stream))
+        assert st == 0, lib.estimator_last_error().decode()
+        stream.synchronize()
+        err = _floored_rel_err(out.cpu().numpy(), ref)
+        assert err <= TOL, f"call {call}: relative error {err:.3e}"
+
+
+def test_static_scratch_refuses_large_plans():
+    lib = _lib()
+    ng, L = 128, 500.0
+    plan = api.Plan(ng, L, synth.default_k1_edges(ng, L, 12), 10, 10, 6, precision="mixed")
+    assert plan.workspace_bytes(1) > lib.estimator_static_scratch_bytes()
+    field = torch.zeros((1, ng, ng, ng), dtype=torch.float32, device="cuda")
+    out = torch.empty(plan.out_shape(1), dtype=torch.float64, device="cuda")
+    st = lib.estimator_estimate_static(plan._h, C.c_void_p(field.data_ptr()), 1, C.c_void_p(out.data_ptr()),
+                                       C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == 1
+    assert "static scratch" in lib.estimator_last_error().decode()
