@@ -110,6 +110,24 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself when
+    no process group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank processes its own units (weak
+    scaling), the job ends with the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def _traffic(ng):
     """DRAM bytes per Step-II launch from the committed ncu summary, if any."""
     p = os.path.join(ROOT, "profiles", "step2_dram.json")
@@ -253,11 +271,8 @@ def run_ours(args):
     st_ms, st_n = plan.stage_times()
     plan.set_timing(False)
     flops = plan.stage_flops()
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * plan.n_bins / (ms / 1e3)
+    ms = max_over_ranks(ms, device=dev)
+    value = job_rate(plan.n_bins, world, ms / 1e3)
     finite = bool(torch.isfinite(out).any().item())
 
     # end to end through the host entry point: pinned field in, B out, copies timed
@@ -270,11 +285,8 @@ def run_ours(args):
     for _ in range(args.steps):
         plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
     te = (time.perf_counter() - te) / args.steps
-    if world > 1:
-        t = torch.tensor([te], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
-    e2e = {"value": world * plan.n_bins / te, "unit": "configs/s",
+    te = max_over_ranks(te, device=dev)
+    e2e = {"value": job_rate(plan.n_bins, world, te), "unit": "configs/s",
            "h2d_bytes_per_step": int(host.numel() * host.element_size()),
            "d2h_bytes_per_step": int(out_h.size * 8)}
 

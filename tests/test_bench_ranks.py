@@ -1,0 +1,53 @@
+"""The multi-rank logic of bench.py on CPU ranks (gloo, world size 2):
+the reported time is the slowest rank's, the throughput counts every
+rank's units (weak scaling), and the estimate path has no collective."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, loc = bench._dist()
+        slow = bench.max_over_ranks(10.0 + 5.0 * rank)
+        rate = bench.job_rate(12000, w, slow)
+        q.put((r, w, loc, slow, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_cpu_ranks():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[0] for o in out] == [0, 1] and all(o[1] == 2 for o in out)
+    assert all(o[3] == 15.0 for o in out)
+    assert all(abs(o[4] - 2 * 12000 / 15.0) < 1e-9 for o in out)
+
+
+def test_single_process_has_no_group():
+    import bench
+    assert bench.max_over_ranks(3.5) == 3.5
+    assert bench.job_rate(100, 1, 2.0) == 50.0
