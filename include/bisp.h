@@ -55,9 +55,11 @@ typedef enum {
 } bisp_status;
 
 typedef enum {
-    BISP_PREC_FP32 = 0,   /* FP32 transforms, products and sums ("plain")          */
-    BISP_PREC_MIXED = 1,  /* FP32 transforms and products, FP64 sums and binning   */
-    BISP_PREC_FP64 = 2    /* FP64 throughout (verification)                         */
+    BISP_PREC_FP32 = 0,     /* FP32 transforms, products and sums ("plain")                */
+    BISP_PREC_MIXED = 1,    /* FP32 transforms and products, FP64 sums and binning         */
+    BISP_PREC_FP64 = 2,     /* FP64 throughout (verification)                               */
+    BISP_PREC_MIXED_TC = 3  /* as MIXED, with the triple sums on the tensor cores: TF32     */
+                            /* mma with each FP32 operand split into two TF32 parts        */
 } bisp_precision;
 
 /* Opaque plan: ring tables, triangle counts, combination tables, bin

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-PRECISIONS = {"fp32": 0, "mixed": 1, "fp64": 2}
+PRECISIONS = {"fp32": 0, "mixed": 1, "fp64": 2, "mixed_tc": 3}
 STATUS = {0: "BISP_OK", 1: "BISP_INVALID_ARG", 2: "BISP_UNSUPPORTED_SIZE", 3: "BISP_OUT_OF_MEMORY",
           4: "BISP_CUDA_ERROR", 5: "BISP_TIMEOUT", 6: "BISP_INTERNAL"}
 

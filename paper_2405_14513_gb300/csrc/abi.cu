@@ -61,6 +61,7 @@ struct bisp_plan {
     std::vector<void *> owned;           // device allocations of the plan
     Group *d_groups = nullptr;
     Tile *d_tiles = nullptr;
+    MTile *d_mtiles = nullptr;
     Unit *d_units = nullptr;
     int64_t *d_doff = nullptr;
     Record *d_rec = nullptr;
@@ -193,7 +194,7 @@ int check_desc(const bisp_desc *d)
     if (d->n_mu < 1 || d->n_t < 1 || d->n_mu > 4096 || d->n_t > 4096)
         return fail(BISP_INVALID_ARG, "n_mu and n_t must be in [1, 4096]");
     if (d->l_max < 0 || d->l_max > 8 || (d->l_max & 1)) return fail(BISP_INVALID_ARG, "l_max must be even, 0..8");
-    if (d->precision < BISP_PREC_FP32 || d->precision > BISP_PREC_FP64)
+    if (d->precision < BISP_PREC_FP32 || d->precision > BISP_PREC_MIXED_TC)
         return fail(BISP_INVALID_ARG, "unknown precision");
     if (d->max_batch < 1) return fail(BISP_INVALID_ARG, "max_batch must be >= 1");
     return BISP_OK;
@@ -335,12 +336,14 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     if (st) return st;
     P.celem = p->celem;
     P.max_cls = desc->precision == BISP_PREC_FP64 ? 3 : 4;   // FP64 blocks have at most 8 warps
+    P.tensor = desc->precision == BISP_PREC_MIXED_TC;       // Step II on tensor cores
     std::string err = enumerate(P, kXChunk);
     if (!err.empty()) return fail(BISP_INTERNAL, err);
     sort_records(P);
 
     st = upload(p, &p->d_groups, P.groups, s);
     if (!st) st = upload(p, &p->d_tiles, P.tiles, s);
+    if (!st) st = upload(p, &p->d_mtiles, P.mtiles, s);
     if (!st) st = upload(p, &p->d_units, P.units, s);
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
@@ -419,7 +422,7 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
     const int64_t ng2 = int64_t(ng) * ng;
     const R scale = R(P.volume / (double(ng2) * ng));
-    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
+    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_mtiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
     for (int b = 0; b < batch; ++b) {
         const R *d = delta + int64_t(b) * ng2 * ng;
         {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
@@ -439,7 +442,7 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
         }
         {   // Step II: triple sums (Eq. fftbs)
             StageMark m(p, BISP_STAGE_STEP2, sizeof(R) == 8 ? 2 : 3, s);
-            CK(launch_step2<R>(a2, dstore, P.class_begin, s));
+            CK(launch_step2<R>(a2, dstore, P.class_begin, P.tensor, s));
         }
         {
             StageMark m(p, BISP_STAGE_REDUCE, 1, s);
@@ -462,6 +465,7 @@ int dispatch_estimate(bisp_plan *p, const void *delta, int batch, void *ws, doub
     case BISP_PREC_FP32:
         return run_estimate<float, float, float, float>(p, static_cast<const float *>(delta), batch, w, B, s);
     case BISP_PREC_MIXED:
+    case BISP_PREC_MIXED_TC:
         return run_estimate<float, float, double, double>(p, static_cast<const float *>(delta), batch, w, B, s);
     default:
         return run_estimate<double, double, double, double>(p, static_cast<const double *>(delta), batch, w, B, s);

@@ -29,7 +29,8 @@ struct Job {
 
 struct StepIIArgs {
     const Group *groups;
-    const Tile *tiles;
+    const Tile *tiles;       // FP64 path
+    const MTile *mtiles;     // FP32 paths (tensor cores)
     const Unit *units;
     const int64_t *doff;     // [kMaxLevels][nz+1][kMaxRings]
     int nz1;                 // planes stored: 0 .. nz1 - 1
@@ -66,9 +67,10 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
 // Step II: partial triple sums of every unit, one block per unit, one launch
 // per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
 // 2^c warps with kStep2ClassSmem[c] bytes of shared memory).
+// tensor: the plan built tensor-core tiles (FP32 paths only).
 template <typename R>
 cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
-                         cudaStream_t s);
+                         bool tensor, cudaStream_t s);
 
 // S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
 template <typename A>

@@ -150,6 +150,106 @@ void enumerate_pair(const HostPlan &P, int n1, int n2, PairOut &out)
     }
 }
 
+// Windows of 8 consecutive r3 covering the set cov (greedy from the lowest);
+// returns their count and writes their first r3 to w0 (when not null).
+int cover_windows(const uint8_t *cov, int ncov, uint8_t *w0)
+{
+    int n = 0;
+    for (int c = 0; c < ncov;) {
+        if (!cov[c]) { ++c; continue; }
+        if (w0 && n < kMWins) w0[n] = uint8_t(c);
+        ++n;
+        c += kTileCols;
+    }
+    return n;
+}
+
+// Tensor-core tiles of one group: rows in the given order, blocks of up to
+// 16 rows whose r3 runs need at most 8 windows; then units of 16, 8 or 4
+// tiles (one per warp) with the rings they stage.
+template <typename UsedFn>
+std::string build_mtiles(HostPlan &P, const Group &G, const Row *rw, const std::vector<int> &order, int lg,
+                         int n1, int n2, int n3, std::vector<Unit> &unit_tmpl, UsedFn &&U_)
+{
+    const int nr = P.rings.nr;
+    struct Blk { int rows[kMRows]; int nr; uint8_t w0[kMWins]; int nwin; };
+    std::vector<Blk> blks;
+    const int ncov = kMaxRings + kTileCols;
+    for (int b = 0; b < G.nrow;) {
+        Blk k{};
+        std::vector<uint8_t> cov(ncov, 0);
+        while (b < G.nrow && k.nr < kMRows) {
+            std::vector<uint8_t> c2 = cov;
+            const Row &r = rw[order[b]];
+            for (int c = 0; c < r.n; ++c) c2[r.r3a + c] = 1;
+            if (k.nr > 0 && cover_windows(c2.data(), ncov, nullptr) > kMWins) break;
+            cov.swap(c2);
+            k.rows[k.nr++] = order[b++];
+        }
+        k.nwin = cover_windows(cov.data(), ncov, k.w0);
+        if (k.nwin > kMWins) return "a row needs more than 8 windows";
+        blks.push_back(k);
+    }
+    size_t u0 = 0;
+    while (u0 < blks.size()) {
+        const size_t rem = blks.size() - u0;
+        int cls = rem > 8 ? 4 : (rem > 4 ? 3 : 2);
+        if (cls > P.max_cls) cls = P.max_cls;
+        const size_t take = std::min(rem, size_t(1) << cls);
+        const size_t u1 = u0 + take;
+        Unit U{};
+        U.t0 = int32_t(P.mtiles.size());
+        U.nt = int32_t(take);
+        int lo[3] = {nr, nr, kMaxRings}, hi[3] = {-1, -1, -1};
+        for (size_t t = u0; t < u1; ++t) {
+            const Blk &k = blks[t];
+            for (int q = 0; q < k.nr; ++q) {
+                const Row &r = rw[k.rows[q]];
+                lo[0] = std::min<int>(lo[0], r.r1); hi[0] = std::max<int>(hi[0], r.r1);
+                lo[1] = std::min<int>(lo[1], r.r2); hi[1] = std::max<int>(hi[1], r.r2);
+            }
+            for (int j = 0; j < k.nwin; ++j) {
+                lo[2] = std::min<int>(lo[2], k.w0[j]);
+                hi[2] = std::max<int>(hi[2], k.w0[j] + kTileCols - 1);
+            }
+        }
+        for (int q = 0; q < 3; ++q) { U.rlo[q] = int16_t(lo[q]); U.rhi[q] = int16_t(hi[q]); }
+        const int nq0 = hi[0] - lo[0] + 1, nq1 = hi[1] - lo[1] + 1, nq2 = hi[2] - lo[2] + 1;
+        const int ns = nq0 + nq1 + nq2;
+        if (ns > 255) return "too many staged rings in a Step-II unit";
+        while (cls < P.max_cls && step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls]) ++cls;
+        if (step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls]) return "Step-II unit too large for shared memory";
+        U.cls = cls;
+        P.max_slots = std::max(P.max_slots, ns);
+        for (size_t t = u0; t < u1; ++t) {
+            const Blk &k = blks[t];
+            MTile T{};
+            for (int q = 0; q < kMRows; ++q) {
+                const Row &r = rw[k.rows[q < k.nr ? q : 0]];
+                T.row[q].s1 = uint8_t(r.r1 - lo[0]);
+                T.row[q].s2 = uint8_t(nq0 + r.r2 - lo[1]);
+                T.row[q].r3a = r.r3a;
+                T.row[q].n = q < k.nr ? r.n : 0;
+                T.row[q].coff = r.coff;
+            }
+            for (int j = 0; j < kMWins; ++j) {
+                const int w = j < k.nwin ? k.w0[j] : k.w0[0];
+                T.w0[j] = uint8_t(w);
+                T.s3[j] = uint8_t(nq0 + nq1 + w - lo[2]);
+            }
+            T.nwin = k.nwin;
+            P.mtiles.push_back(T);
+        }
+        const int nsabs[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
+        for (int q = 0; q < 3; ++q)
+            for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lg, nsabs[q], r) = 1;
+        U.group = int32_t(P.groups.size());
+        unit_tmpl.push_back(U);
+        u0 = u1;
+    }
+    return "";
+}
+
 }  // namespace
 
 std::string enumerate(HostPlan &P, int64_t x_chunk)
@@ -191,6 +291,7 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     P.groups.clear();
     P.rows.clear();
     P.tiles.clear();
+    P.mtiles.clear();
     P.units.clear();
     P.records_s.clear();
     P.ntri_s.clear();
@@ -283,6 +384,13 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                     raws.push_back(t);
                     for (int d = 0; d < kTileCols; ++d) cov[c + d] = 0;
                 }
+            }
+            if (P.tensor) {
+                std::string e = build_mtiles(P, G, rw, order, lg, n1, n2, n3, unit_tmpl, U_);
+                if (!e.empty()) return e;
+                P.groups.push_back(G);
+                group_unit0.push_back(int32_t(unit_tmpl.size()));
+                continue;
             }
             // units: runs of 16, 8 or 4 consecutive tiles (one per warp), each
             // staging the union of its tiles' rings

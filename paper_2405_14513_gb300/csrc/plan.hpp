@@ -66,6 +66,25 @@ struct Tile {
 };
 static_assert(sizeof(Tile) == 64, "Tile is copied in 16-byte pieces");
 
+// Tensor-core Step-II tile: up to 16 rows of one group times up to 8 windows
+// of 8 consecutive r3 (each placed where the rows need it).  Row i's
+// combinations are (r3a .. r3a + n - 1) -> coff .. coff + n - 1; padding rows
+// have n = 0.
+struct MRow {
+    uint8_t s1, s2, r3a, n;    // staged slots of D(r1, n1), D(r2, n2); r3 run
+    int32_t coff;
+};
+constexpr int kMRows = 16;
+constexpr int kMWins = 8;
+struct MTile {
+    MRow row[kMRows];
+    uint8_t s3[kMWins];        // staged slot of the first r3 of each window
+    uint8_t w0[kMWins];        // first r3 of each window
+    int32_t nwin;
+    int32_t pad[3];
+};
+static_assert(sizeof(MTile) == 160, "MTile is copied in 16-byte pieces");
+
 // One Step-II block: an x chunk of a group with up to 16 of its tiles (one
 // per warp), and the ring ranges it stages per plane (plane 3 may reach
 // past the last ring; those slots are zero).  cls: log2 of the warps of the
@@ -118,7 +137,9 @@ struct HostPlan {
     // combinations in S order
     std::vector<Group> groups;
     std::vector<Row> rows;
-    std::vector<Tile> tiles;
+    std::vector<Tile> tiles;            // FP64 path: 8 x 8 register tiles
+    std::vector<MTile> mtiles;          // FP32 paths: 16-row tensor-core tiles
+    bool tensor = false;                // build mtiles (set before enumerate)
     std::vector<Unit> units;            // Step-II blocks in launch order
     int max_slots = 0;                  // largest staged ring count of a unit
     int max_cls = 4;                    // largest block class (set before enumerate)

@@ -43,6 +43,7 @@ def test_status_strings():
     (dict(n_mu=0), 1),
     (dict(n_t=-1), 1),
     (dict(precision=7), 1),
+    (dict(precision=-1), 1),
     (dict(max_batch=0), 1),
     (dict(box_len=0.0), 1),
     (dict(box_len=float("nan")), 1),

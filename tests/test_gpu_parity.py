@@ -25,7 +25,7 @@ if not torch.cuda.is_available():
 
 from paper_2405_14513_gb300 import api  # noqa: E402
 
-TOL = {"fp32": 1e-4, "mixed": 1e-4, "fp64": 1e-10}
+TOL = {"fp32": 1e-4, "mixed": 1e-4, "mixed_tc": 1e-4, "fp64": 1e-10}
 
 
 def floored_rel_err(got, ref):
@@ -140,11 +140,17 @@ def test_multipoles_match_oracle(which, c64, c64_fp64):
     assert err.max() < TOL[which], err
 
 
-def test_fp32_plain_path():
-    c = Case(64, 1000.0, 6, 5, 5, 6, precision="fp32", seed=2)
+@pytest.mark.parametrize("prec", ["fp32", "mixed_tc"])
+def test_fp32_plain_and_tensor_core_paths(prec):
+    c = Case(64, 1000.0, 6, 5, 5, 6, precision=prec, seed=2)
     ref = O.select_even(c.oracle["B"], c.l_max)
     err = floored_rel_err(c.B, ref)
-    assert err.max() < TOL["fp32"], err
+    assert err.max() < TOL[prec], err
+    tab = c.plan.combo_table()
+    S = c.plan.combo_sums(c.ws)
+    pick = np.random.default_rng(8).choice(len(S), size=300, replace=False)
+    want = O.combo_sums(c.field64, c.L, tab["ints"][pick]).real
+    assert np.abs(S[pick] - want).max() < TOL[prec] * np.sqrt(np.mean(want ** 2))
 
 
 def test_brute_force_16():
