@@ -205,15 +205,18 @@ int estimator_denominator(const bisp_plan *plan, double *den);
 int64_t estimator_combo_table(const bisp_plan *plan, int64_t cap, int32_t *ints, int64_t *ntri,
                               int32_t *bin, int32_t *grid);
 
-/* After estimator_estimate on this workspace: the complex sums
+/* After estimator_estimate on this workspace: the real parts of the sums
  * S = sum_x D1 D2 D3 of Eq. fftbs (full N_g^2 grid normalisation) of the last
- * field of the batch, in estimator_combo_table order.  S: HOST pointer
- * [n_combos][2].  Synchronises `stream`. */
+ * field of the batch, in estimator_combo_table order (the imaginary parts
+ * cancel between the members of each +-n pair and are not formed).  S: HOST
+ * pointer [n_combos].  Synchronises `stream`. */
 int estimator_combo_sums(const bisp_plan *plan, const void *workspace, double *S, void *stream);
 
 /* After estimator_estimate on this workspace: D(r, n, x) of Eq. iFT of the
- * last field, sampled on the M x M grid x = (N_g/M) y, as stored for the
- * Step-II reduction.  out: HOST pointer [M][M][2] (y_x slow, y_y fast), in
+ * last field at the M x M points x = (N_g/M) y, y integer, i.e.
+ * sum_{u in r} Delta(u, n) exp(-2 pi i u.y / M), as stored for the Step-II
+ * reduction.  M is one of the plan's reduction grid sides (2^q or 3 x 2^q,
+ * 8 <= M <= N_g).  out: HOST pointer [M][M][2] (y_x slow, y_y fast), in
  * double.  Returns BISP_INVALID_ARG when (M, n, r) is not stored. */
 int estimator_dfield(const bisp_plan *plan, const void *workspace, int M, int n, int r,
                      double *out, void *stream);

@@ -340,6 +340,44 @@ int bo_dfield(int ng, double box_len, const double *delta, int r, int n, double 
     return 0;
 }
 
+/* exported: D(r, n, x) of Eq. iFT at the M x M points x = (N_g/M) y, y
+ * integer: sum over the ring's members u of Delta(u, n) exp(-2 pi i u.y / M),
+ * summed directly (one axis after the other) for any M >= 1.  out [M][M][2]. */
+int bo_dfield_at(int ng, double box_len, const double *delta, int r, int n, int M, double *out_re_im)
+{
+    if (M < 1) return -1;
+    rings_t R;
+    if (rings_build(ng, &R)) return -1;
+    cplx *cube = forward_cube(ng, box_len, delta);
+    long kz = ((n % ng) + ng) % ng;
+    /* e[a][y] = exp(-2 pi i u_a y / M), u_a the signed frequency of index a */
+    cplx *e = malloc(sizeof(cplx) * (size_t)ng * M);
+    for (long a = 0; a < ng; ++a)
+        for (long y = 0; y < M; ++y) {
+            double ph = -BO_TWO_PI * (double)((signed_freq(a, ng) * y) % M) / (double)M;
+            e[a * M + y] = cos(ph) + I * sin(ph);
+        }
+    cplx *t = calloc((size_t)ng * M, sizeof(cplx));     /* t[a][y_y] */
+    for (long a = 0; a < ng; ++a)
+        for (long b = 0; b < ng; ++b) {
+            if (rings_at(&R, signed_freq(a, ng), signed_freq(b, ng)) != r) continue;
+            cplx v = cube[(a * ng + b) * ng + kz];
+            for (long y = 0; y < M; ++y) t[a * M + y] += v * e[b * M + y];
+        }
+    for (long yx = 0; yx < M; ++yx)
+        for (long yy = 0; yy < M; ++yy) {
+            cplx s = 0;
+            for (long a = 0; a < ng; ++a) s += e[a * M + yx] * t[a * M + yy];
+            out_re_im[2 * (yx * M + yy)] = creal(s);
+            out_re_im[2 * (yx * M + yy) + 1] = cimag(s);
+        }
+    free(t);
+    free(e);
+    free(cube);
+    free(R.ringidx);
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Triangle counts: Eq. Ntri2 (FFT of unit fields) or Eq. Ntri1 (count).     */
 /* table[(r1*nr + r2)*nr + r3].                                              */

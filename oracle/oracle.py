@@ -56,6 +56,7 @@ def _load():
             lib.bo_rings.restype = C.c_int
             lib.bo_forward.argtypes = [C.c_int, C.c_double, dp, dp]
             lib.bo_dfield.argtypes = [C.c_int, C.c_double, dp, C.c_int, C.c_int, dp]
+            lib.bo_dfield_at.argtypes = [C.c_int, C.c_double, dp, C.c_int, C.c_int, C.c_int, dp]
             lib.bo_ntri.argtypes = [C.c_int, C.c_int, C.c_int, lp]
             lib.bo_ntri.restype = C.c_double
             lib.bo_ylm.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp]
@@ -139,6 +140,17 @@ def dfield(delta: np.ndarray, box_len: float, r: int, n: int) -> np.ndarray:
     out = np.zeros((ng, ng, 2))
     if _load().bo_dfield(ng, box_len, _dp(d), r, n, _dp(out)):
         raise RuntimeError("bo_dfield failed")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def dfield_at(delta: np.ndarray, box_len: float, r: int, n: int, M: int) -> np.ndarray:
+    """D(r, n, x) of Eq. iFT at x = (N_g/M) y for integer y on an M x M grid,
+    summed directly over the ring's modes; complex [M][M]."""
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    ng = d.shape[0]
+    out = np.zeros((M, M, 2))
+    if _load().bo_dfield_at(ng, box_len, _dp(d), r, n, M, _dp(out)):
+        raise RuntimeError("bo_dfield_at failed")
     return out[..., 0] + 1j * out[..., 1]
 
 

@@ -68,9 +68,9 @@ struct bisp_plan {
     int64_t *d_bin_start = nullptr;
     double *d_den = nullptr;
     std::vector<double> h_den;
-    float2 *d_tw_f = nullptr;
-    double2 *d_tw_d = nullptr;
-    int lg_tw = 0;
+    Twiddles<float2> tw_f{};             // transform twiddles (device tables)
+    Twiddles<double2> tw_d{};
+    GridArg grid_arg{};                  // reduction grid sides by level index
     RingArg ring_arg{};
     std::vector<Job *> d_jobs;           // per level in use
     std::vector<int64_t *> d_job_off;    // per level: output offsets of the jobs
@@ -212,22 +212,23 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
     for (int a = 0; a < nr; ++a)
         for (int b = a; b < nr; ++b)
             for (int c = b; c < nr; ++c) {
-                int lg = triple_log2m(R, a, b, c);
-                tri.insert(tri.end(), {a, b, c, lg});
-                need[lg * kMaxRings + a] = need[lg * kMaxRings + b] = need[lg * kMaxRings + c] = 1;
+                const int lv = triple_level(R, a, b, c);
+                tri.insert(tri.end(), {a, b, c, lv});
+                need[lv * kMaxRings + a] = need[lv * kMaxRings + b] = need[lv * kMaxRings + c] = 1;
             }
     std::vector<int64_t> ioff(size_t(kMaxLevels) * kMaxRings, -1);
     int64_t cur = 0, gtmax = 0;
     std::vector<std::vector<Job>> jobs(kMaxLevels);
-    for (int lg = kMinLog2M; lg < kMaxLevels; ++lg)
+    for (int lv = 0; lv < R.ngrid; ++lv) {
+        const int64_t M2 = int64_t(R.grid[lv]) * R.grid[lv];
         for (int r = 0; r < nr; ++r)
-            if (need[lg * kMaxRings + r]) {
-                ioff[lg * kMaxRings + r] = cur;
-                jobs[lg].push_back(Job{0, r, cur});
-                cur += int64_t(1) << (2 * lg);
+            if (need[lv * kMaxRings + r]) {
+                ioff[lv * kMaxRings + r] = cur;
+                jobs[lv].push_back(Job{0, r, cur});
+                cur += M2;
             }
-    for (int lg = kMinLog2M; lg < kMaxLevels; ++lg)
-        gtmax = std::max<int64_t>(gtmax, int64_t(jobs[lg].size()) << (2 * lg));
+        gtmax = std::max<int64_t>(gtmax, int64_t(jobs[lv].size()) * M2);
+    }
 
     std::vector<void *> tmp;
     auto talloc = [&](size_t bytes) -> void * {
@@ -251,20 +252,19 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
     auto run = [&]() -> int {
         CK(cudaMemcpyAsync(d_ioff, ioff.data(), ioff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(d_tri, tri.data(), tri.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        for (int lg = kMinLog2M; lg < kMaxLevels; ++lg) {
-            if (jobs[lg].empty()) continue;
-            const int M = 1 << lg;
+        for (int lv = 0; lv < R.ngrid; ++lv) {
+            if (jobs[lv].empty()) continue;
+            const int M = R.grid[lv];
             std::vector<int64_t> joff;
-            for (auto &j : jobs[lg]) joff.push_back(j.out_off);
-            CK(cudaMemcpyAsync(d_jobs, jobs[lg].data(), jobs[lg].size() * sizeof(Job), cudaMemcpyHostToDevice, s));
+            for (auto &j : jobs[lv]) joff.push_back(j.out_off);
+            CK(cudaMemcpyAsync(d_jobs, jobs[lv].data(), jobs[lv].size() * sizeof(Job), cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(d_joff, joff.data(), joff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
-            CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lg].size()), M, true, gt,
-                                          p->d_tw_d, p->lg_tw, s));
-            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lg].size()), d_joff, 1.0, false, p->d_tw_d,
-                                         p->lg_tw, s));
+            CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lv].size()), M, true, gt,
+                                          p->tw_d, s));
+            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lv].size()), d_joff, 1.0, false, p->tw_d, s));
             CK(cudaStreamSynchronize(s));   // the job tables are reused by the next grid
         }
-        CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), d_raw, s));
+        CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), p->grid_arg, d_raw, s));
         std::vector<double> raw(tri.size() / 4);
         CK(cudaMemcpyAsync(raw.data(), d_raw, raw.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -304,20 +304,29 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     for (int r = 0; r <= R.nr; ++r) p->ring_arg.e3sq[r] = R.e3[r] * R.e3[r];
     for (int r = 0; r < R.nr; ++r) p->ring_arg.maxc[r] = R.maxc[r];
 
-    // twiddles exp(-2 pi i k / N_g), k < N_g / 2, in double
-    p->lg_tw = ilog2i(desc->n_g);
+    for (int l = 0; l < R.ngrid; ++l) p->grid_arg.M[l] = R.grid[l];
+    // twiddles in double: exp(-2 pi i k / N_g), k < N_g / 2, for the lengths
+    // 2^q, and exp(-2 pi i k / (3 N_g / 2)), k < 3 N_g / 4, for 3 x 2^q
     {
-        const int h = desc->n_g / 2;
-        std::vector<double2> twd(h);
-        std::vector<float2> twf(h);
-        for (int k = 0; k < h; ++k) {
-            const double a = -kTwoPi * double(k) / double(desc->n_g);
-            twd[k] = make_double2(std::cos(a), std::sin(a));
-            twf[k] = make_float2(float(twd[k].x), float(twd[k].y));
-        }
-        int st = upload(p, &p->d_tw_d, twd, s);
-        if (!st) st = upload(p, &p->d_tw_f, twf, s);
+        const int lg2 = ilog2i(desc->n_g);
+        auto table = [&](int base, int count, float2 **df, double2 **dd) -> int {
+            std::vector<double2> twd(count);
+            std::vector<float2> twf(count);
+            for (int k = 0; k < count; ++k) {
+                const double a = -kTwoPi * double(k) / double(base);
+                twd[k] = make_double2(std::cos(a), std::sin(a));
+                twf[k] = make_float2(float(twd[k].x), float(twd[k].y));
+            }
+            int st = upload(p, dd, twd, s);
+            return st ? st : upload(p, df, twf, s);
+        };
+        float2 *f2 = nullptr, *f3 = nullptr;
+        double2 *d2 = nullptr, *d3 = nullptr;
+        int st = table(desc->n_g, desc->n_g / 2, &f2, &d2);
+        if (!st) st = table(3 * desc->n_g / 2, 3 * desc->n_g / 4, &f3, &d3);
         if (st) return st;
+        p->tw_f = Twiddles<float2>{f2, f3, lg2, lg2 - 1};
+        p->tw_d = Twiddles<double2>{d2, d3, lg2, lg2 - 1};
     }
     // Y_lm normalisations
     {
@@ -378,7 +387,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
         std::vector<int64_t> off;
         for (int n = 0; n <= R.nz; ++n)
             for (int r = 0; r < R.nr; ++r) {
-                int64_t o = P.doff[(size_t(L.log2m) * (R.nz + 1) + n) * kMaxRings + r];
+                int64_t o = P.doff[(size_t(L.lev) * (R.nz + 1) + n) * kMaxRings + r];
                 if (o >= 0) {
                     jobs.push_back(Job{n, r, o});
                     off.push_back(o);
@@ -413,7 +422,8 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     const HostPlan &P = p->hp;
     const Rings &Rg = P.rings;
     const int ng = P.desc.n_g;
-    const C *tw = reinterpret_cast<const C *>(sizeof(R) == 8 ? (const void *)p->d_tw_d : (const void *)p->d_tw_f);
+    Twiddles<C> tw;
+    if constexpr (sizeof(R) == 8) tw = p->tw_d; else tw = p->tw_f;
     C *A_ = reinterpret_cast<C *>(ws + p->off_a);
     C *B_ = reinterpret_cast<C *>(ws + p->off_b);
     C *gt = reinterpret_cast<C *>(ws + p->off_gt);
@@ -427,17 +437,17 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
         const R *d = delta + int64_t(b) * ng2 * ng;
         {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
             StageMark m(p, BISP_STAGE_FORWARD, 3, s);
-            CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, p->lg_tw, s));
-            CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, p->lg_tw, s));
-            CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, p->lg_tw, s));
+            CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, s));
+            CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, s));
+            CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, s));
         }
         {   // Step I: D(r, n) on each reduction grid (Eq. iFT)
             StageMark m(p, BISP_STAGE_STEP1, int(2 * P.levels.size()), s);
             for (size_t l = 0; l < P.levels.size(); ++l) {
                 const Level &L = P.levels[l];
-                const int M = 1 << L.log2m;
-                CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, p->lg_tw, s));
-                CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, p->lg_tw, s));
+                const int M = L.M;
+                CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, s));
+                CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, s));
             }
         }
         {   // Step II: triple sums (Eq. fftbs)
@@ -596,8 +606,8 @@ int estimator_stage_flops(const bisp_plan *p, double *flops)
     flops[BISP_STAGE_FORWARD] = 5.0 * ng * lg * (ng * ng + 2.0 * planes * ng);
     double s1 = 0;
     for (const Level &L : P.levels) {
-        const double M = double(1 << L.log2m);
-        s1 += double(L.njobs) * 2.0 * M * 5.0 * M * L.log2m;
+        const double M = double(L.M);
+        s1 += double(L.njobs) * 2.0 * M * 5.0 * M * std::log2(M);
     }
     flops[BISP_STAGE_STEP1] = s1;
     flops[BISP_STAGE_STEP2] = 4.0 * P.triple_products + 6.0 * P.pair_products;
@@ -649,7 +659,7 @@ int64_t estimator_combo_table(const bisp_plan *p, int64_t cap, int32_t *ints, in
                 }
                 if (ntri) ntri[k] = P.ntri[(size_t(q.r1) * nr + q.r2) * nr + r3];
                 if (bin) bin[k] = P.combo_bin[k];
-                if (grid) grid[k] = 1 << G.log2m;
+                if (grid) grid[k] = G.M;
             }
         }
     return P.n_combos;
@@ -683,10 +693,12 @@ int estimator_dfield(const bisp_plan *p, const void *workspace, int M, int n, in
 {
     if (!p || !workspace || !out) return fail(BISP_INVALID_ARG, "NULL argument");
     const HostPlan &P = p->hp;
-    if (M < 8 || (M & (M - 1)) || M > P.desc.n_g || n < 0 || n > P.rings.nz || r < 0 || r >= P.rings.nr)
+    int lv = -1;
+    for (int l = 0; l < P.rings.ngrid; ++l)
+        if (P.rings.grid[l] == M) lv = l;
+    if (lv < 0 || n < 0 || n > P.rings.nz || r < 0 || r >= P.rings.nr)
         return fail(BISP_INVALID_ARG, "no such field");
-    const int lg = ilog2i(M);
-    const int64_t o = P.doff[(size_t(lg) * (P.rings.nz + 1) + n) * kMaxRings + r];
+    const int64_t o = P.doff[(size_t(lv) * (P.rings.nz + 1) + n) * kMaxRings + r];
     if (o < 0) return fail(BISP_INVALID_ARG, "field not stored on this grid");
     const unsigned char *src = static_cast<const unsigned char *>(workspace) + p->off_dstore + size_t(o) * p->celem;
     return copy_complex_out(p, src, int64_t(M) * M, out, static_cast<cudaStream_t>(stream));

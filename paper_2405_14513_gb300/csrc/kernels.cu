@@ -13,8 +13,10 @@
 //                   Eq. bs_lm2_1; or the plan-time denominators
 //   k_ntri          N_tri = M^-2 sum_y I1 I2 I3 on the unit fields (Eq. Ntri2)
 //
-// All transforms use exp(-i k.x), the sign of Eq. iFT, with twiddles
-// tw[k] = exp(-2 pi i k / 2^lg_tw) computed on the host in double.
+// All transforms use exp(-i k.x), the sign of Eq. iFT.  Transform lengths
+// are 2^q or 3 x 2^q (the reduction grids of the plan); the twiddle tables,
+// computed on the host in double, are tw2[k] = exp(-2 pi i k / 2^lg2) and
+// tw3[k] = exp(-2 pi i k / (3 x 2^lg3)).
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -41,25 +43,52 @@ template <typename C> __device__ __forceinline__ C cmk(double re, double im);
 template <> __device__ __forceinline__ float2 cmk<float2>(double re, double im) { return make_float2(float(re), float(im)); }
 template <> __device__ __forceinline__ double2 cmk<double2>(double re, double im) { return make_double2(re, im); }
 
-// Stockham radix-2 transform of nrows rows of length 2^lg held in shared
-// memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M).  Every thread
+// Stockham transform of nrows rows of length M = 2^q or 3 x 2^q held in
+// shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M): one
+// radix-3 stage first when 3 divides M, then radix-2 stages.  Every thread
 // of the block takes part; the caller synchronises before the call.  The
 // result is in the returned buffer (a or b).
 template <typename C>
-__device__ C *fft_smem(C *a, C *b, int lg, int P, int nrows, const C *__restrict__ tw, int lg_tw)
+__device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
 {
-    const int half = 1 << (lg - 1);
-    const int total = nrows << (lg - 1);
-    for (int s = 0; s < lg; ++s) {
-        const int Ns = 1 << s;
-        const int tws = lg_tw - s - 1;
+    using Rr = decltype(a[0].x);
+    const bool has3 = (M % 3) == 0;
+    int Ns = 1;
+    if (has3) {
+        const int third = M / 3;
+        const int total = nrows * third;
+        const Rr h = Rr(0.86602540378443864676);   // sqrt(3)/2
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int row = t >> (lg - 1);
-            const int j = t & (half - 1);
-            const int k = j & (Ns - 1);
+            const int row = t / third, j = t - row * third;
+            const C v0 = a[row * P + j], v1 = a[row * P + j + third], v2 = a[row * P + j + 2 * third];
+            const Rr sx = v1.x + v2.x, sy = v1.y + v2.y, dx = v1.x - v2.x, dy = v1.y - v2.y;
+            const Rr mx = v0.x - Rr(0.5) * sx, my = v0.y - Rr(0.5) * sy;
+            C y0, y1, y2;
+            y0.x = v0.x + sx; y0.y = v0.y + sy;
+            y1.x = mx + h * dy; y1.y = my - h * dx;
+            y2.x = mx - h * dy; y2.y = my + h * dx;
+            b[row * P + 3 * j] = y0;
+            b[row * P + 3 * j + 1] = y1;
+            b[row * P + 3 * j + 2] = y2;
+        }
+        __syncthreads();
+        C *t2 = a;
+        a = b;
+        b = t2;
+        Ns = 3;
+    }
+    const int half = M / 2;
+    const int total = nrows * half;
+    for (int s = 0; Ns < M; ++s, Ns *= 2) {
+        // twiddle exp(-2 pi i k / (2 Ns)) from the table of the matching family
+        const C *wt = has3 ? tw.tw3 : tw.tw2;
+        const int sh = (has3 ? tw.lg3 : tw.lg2) - s - 1;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int row = t / half, j = t - row * half;
+            const int q = j / Ns, k = j - q * Ns;
             C v0 = a[row * P + j];
-            C v1 = cmul(a[row * P + j + half], __ldg(&tw[k << tws]));
-            const int idx = ((j >> s) << (s + 1)) + k;
+            C v1 = cmul(a[row * P + j + half], __ldg(&wt[k << sh]));
+            const int idx = q * 2 * Ns + k;
             b[row * P + idx] = cadd(v0, v1);
             b[row * P + idx + Ns] = csub(v0, v1);
         }
@@ -74,22 +103,22 @@ __device__ C *fft_smem(C *a, C *b, int lg, int P, int nrows, const C *__restrict
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int lg, int64_t rows,
-             int nkeep, int rt, const typename Cx<R>::T *__restrict__ tw, int lg_tw)
+k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M, int64_t rows,
+             int nkeep, int rt, Twiddles<typename Cx<R>::T> tw)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = 1 << lg, P = M + 1;
+    const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t row0 = int64_t(blockIdx.x) * rt;
     const int nrow = int(min(int64_t(rt), rows - row0));
     for (int t = threadIdx.x; t < nrow * M; t += blockDim.x) {
-        const int r = t >> lg, j = t & (M - 1);
+        const int r = t / M, j = t - r * M;
         a[r * P + j] = cmk<C>(double(in[(row0 + r) * M + j]), 0.0);
     }
     __syncthreads();
-    const C *res = fft_smem(a, b, lg, P, nrow, tw, lg_tw);
+    const C *res = fft_smem(a, b, M, P, nrow, tw);
     for (int t = threadIdx.x; t < nkeep * nrow; t += blockDim.x) {
         const int k = t / nrow, r = t - k * nrow;
         out[int64_t(k) * rows + row0 + r] = res[r * P + k];
@@ -98,13 +127,13 @@ k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int 
 
 template <typename R>
 __global__ void __launch_bounds__(256)
-k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restrict__ out, int lg,
+k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M,
              int nrow, int ntile, const int64_t *__restrict__ out_off, R scale, int zero_dc, int rt,
-             const typename Cx<R>::T *__restrict__ tw, int lg_tw)
+             Twiddles<typename Cx<R>::T> tw)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = 1 << lg, P = M + 1;
+    const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t bt = blockIdx.x / ntile;
@@ -113,11 +142,11 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
     const int nr = min(rt, nrow - row0);
     const C *src = in + bt * int64_t(M) * nrow;
     for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
-        const int r = t >> lg, j = t & (M - 1);
+        const int r = t / M, j = t - r * M;
         a[r * P + j] = src[int64_t(row0 + r) * M + j];
     }
     __syncthreads();
-    const C *res = fft_smem(a, b, lg, P, nr, tw, lg_tw);
+    const C *res = fft_smem(a, b, M, P, nr, tw);
     C *dst = out + (out_off ? out_off[bt] : bt * int64_t(M) * nrow);
     for (int t = threadIdx.x; t < M * nr; t += blockDim.x) {
         const int k = t / nr, r = t - k * nr;
@@ -132,12 +161,12 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
 template <typename R, bool UNIT>
 __global__ void __launch_bounds__(256)
 k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg rings,
-              const Job *__restrict__ jobs, int lg, int ntile, int rt, typename Cx<R>::T *__restrict__ gt,
-              const typename Cx<R>::T *__restrict__ tw, int lg_tw)
+              const Job *__restrict__ jobs, int M, int ntile, int rt, typename Cx<R>::T *__restrict__ gt,
+              Twiddles<typename Cx<R>::T> tw)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int M = 1 << lg, P = M + 1;
+    const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t jb = blockIdx.x / ntile;
@@ -149,7 +178,8 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     const int row0 = tile * rt;
     const int nr = min(rt, M - row0);
     for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
-        const int i = row0 + (t >> lg), j = t & (M - 1);
+        const int tr = t / M, j = t - tr * M;
+        const int i = row0 + tr;
         R vr = 0, vi = 0;
         // members u with u_x = i or i - M and u_y = j or j - M (mod M folding;
         // |u_x|, |u_y| <= maxc < M, so no other alias exists)
@@ -172,10 +202,10 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
                 }
             }
         }
-        a[(t >> lg) * P + j] = cmk<C>(double(vr), double(vi));
+        a[tr * P + j] = cmk<C>(double(vr), double(vi));
     }
     __syncthreads();
-    const C *res = fft_smem(a, b, lg, P, nr, tw, lg_tw);
+    const C *res = fft_smem(a, b, M, P, nr, tw);
     C *dst = gt + jb * int64_t(M) * M;
     for (int t = threadIdx.x; t < M * nr; t += blockDim.x) {
         const int k = t / nr, r = t - k * nr;
@@ -214,8 +244,8 @@ k_step2(StepIIArgs args, int64_t unit0, const typename Cx<R>::T *__restrict__ ds
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Unit U = args.units[unit0 + blockIdx.x];
     const Group G = args.groups[U.group];
-    const int lg = G.log2m;
-    const int64_t M2 = int64_t(1) << (2 * lg);
+    const int lev = G.lev;
+    const int64_t M2 = int64_t(G.M) * G.M;
     const int64_t x0 = int64_t(U.chunk) * args.x_chunk;
     const int64_t x1 = min(M2, x0 + args.x_chunk);
     const int nq0 = U.rhi[0] - U.rlo[0] + 1, nq1 = U.rhi[1] - U.rlo[1] + 1, nq2 = U.rhi[2] - U.rlo[2] + 1;
@@ -233,7 +263,7 @@ k_step2(StepIIArgs args, int64_t unit0, const typename Cx<R>::T *__restrict__ ds
         const int q = s < nq0 ? 0 : (s < nq0 + nq1 ? 1 : 2);
         const int r = U.rlo[q] + s - (q == 0 ? 0 : (q == 1 ? nq0 : nq0 + nq1));
         const int n = q == 0 ? G.n1 : (q == 1 ? G.n2 : G.n3);
-        offs[s] = r < args.nr ? args.doff[(size_t(lg) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
+        offs[s] = r < args.nr ? args.doff[(size_t(lev) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
     }
     __syncthreads();
 
@@ -340,7 +370,7 @@ __global__ void __launch_bounds__(256)
 k_reduce(const Group *__restrict__ groups, const double *__restrict__ partials, int ng, double *__restrict__ S)
 {
     const Group G = groups[blockIdx.x];
-    const double f = double(ng) / double(1 << G.log2m);
+    const double f = double(ng) / double(G.M);
     const A scale = A(f * f);
     for (int j = threadIdx.x; j < G.ncombo; j += blockDim.x) {
         A s = A(0);
@@ -423,15 +453,15 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
 
 __global__ void __launch_bounds__(256)
 k_ntri(const double2 *__restrict__ I, const int64_t *__restrict__ ioff, const int32_t *__restrict__ tri,
-       double *__restrict__ raw)
+       GridArg grids, double *__restrict__ raw)
 {
     __shared__ double red[8];
     const int r1 = tri[4 * blockIdx.x], r2 = tri[4 * blockIdx.x + 1], r3 = tri[4 * blockIdx.x + 2];
-    const int lg = tri[4 * blockIdx.x + 3];
-    const int64_t M2 = int64_t(1) << (2 * lg);
-    const double2 *a = I + ioff[lg * kMaxRings + r1];
-    const double2 *b = I + ioff[lg * kMaxRings + r2];
-    const double2 *c = I + ioff[lg * kMaxRings + r3];
+    const int lev = tri[4 * blockIdx.x + 3];
+    const int64_t M2 = int64_t(grids.M[lev]) * grids.M[lev];
+    const double2 *a = I + ioff[lev * kMaxRings + r1];
+    const double2 *b = I + ioff[lev * kMaxRings + r2];
+    const double2 *c = I + ioff[lev * kMaxRings + r3];
     double s = 0;
     for (int64_t y = threadIdx.x; y < M2; y += blockDim.x) {
         const double2 p = cmul(cmul(a[y], b[y]), c[y]);
@@ -454,13 +484,6 @@ cudaError_t set_smem(F f, size_t bytes)
     return cudaSuccess;
 }
 
-int ilog2(int v)
-{
-    int l = 0;
-    while ((1 << l) < v) ++l;
-    return l;
-}
-
 }  // namespace
 
 size_t fft_rows_per_block(int M, size_t elem)
@@ -473,26 +496,24 @@ size_t fft_rows_per_block(int M, size_t elem)
 
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    const int lg = ilog2(ng);
     const int rt = int(fft_rows_per_block(ng, sizeof(C)));
     const size_t smem = size_t(2) * rt * (ng + 1) * sizeof(C);
     cudaError_t e = set_smem(k_fft_z_real<R>, smem);
     if (e != cudaSuccess) return e;
     const int64_t nblk = (rows + rt - 1) / rt;
-    k_fft_z_real<R><<<unsigned(nblk), 256, smem, s>>>(in, out, lg, rows, nkeep, rt, tw, lg_tw);
+    k_fft_z_real<R><<<unsigned(nblk), 256, smem, s>>>(in, out, ng, rows, nkeep, rt, tw);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    const int lg = ilog2(M);
     const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(nrow)));
     const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
     cudaError_t e = set_smem(k_fft_rows_T<R>, smem);
@@ -500,18 +521,17 @@ cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *ou
     const int ntile = (nrow + rt - 1) / rt;
     const int64_t nblk = nb * ntile;
     if (nblk == 0) return cudaSuccess;
-    k_fft_rows_T<R><<<unsigned(nblk), 256, smem, s>>>(in, out, lg, nrow, ntile, out_off, scale, zero_dc ? 1 : 0,
-                                                      rt, tw, lg_tw);
+    k_fft_rows_T<R><<<unsigned(nblk), 256, smem, s>>>(in, out, M, nrow, ntile, out_off, scale, zero_dc ? 1 : 0,
+                                                      rt, tw);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings, const Job *jobs,
                                int64_t njobs, int M, bool unit, typename Cx<R>::T *gt,
-                               const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s)
+                               const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
-    const int lg = ilog2(M);
     const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(M)));
     const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
     const int ntile = (M + rt - 1) / rt;
@@ -521,11 +541,11 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     if (unit) {
         e = set_smem(k_ring_gather<R, true>, smem);
         if (e != cudaSuccess) return e;
-        k_ring_gather<R, true><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, lg, ntile, rt, gt, tw, lg_tw);
+        k_ring_gather<R, true><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw);
     } else {
         e = set_smem(k_ring_gather<R, false>, smem);
         if (e != cudaSuccess) return e;
-        k_ring_gather<R, false><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, lg, ntile, rt, gt, tw, lg_tw);
+        k_ring_gather<R, false><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw);
     }
     return cudaGetLastError();
 }
@@ -570,8 +590,8 @@ k_step2_mma(StepIIArgs args, int64_t unit0, const float2 *__restrict__ dstore, i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const Unit U = args.units[unit0 + blockIdx.x];
     const Group G = args.groups[U.group];
-    const int lg = G.log2m;
-    const int64_t M2 = int64_t(1) << (2 * lg);
+    const int lev = G.lev;
+    const int64_t M2 = int64_t(G.M) * G.M;
     const int64_t x0 = int64_t(U.chunk) * args.x_chunk;
     const int64_t x1 = min(M2, x0 + args.x_chunk);
     const int nq0 = U.rhi[0] - U.rlo[0] + 1, nq1 = U.rhi[1] - U.rlo[1] + 1, nq2 = U.rhi[2] - U.rlo[2] + 1;
@@ -591,7 +611,7 @@ k_step2_mma(StepIIArgs args, int64_t unit0, const float2 *__restrict__ dstore, i
         const int q = s < nq0 ? 0 : (s < nq0 + nq1 ? 1 : 2);
         const int r = U.rlo[q] + s - (q == 0 ? 0 : (q == 1 ? nq0 : nq0 + nq1));
         const int n = q == 0 ? G.n1 : (q == 1 ? G.n2 : G.n3);
-        offs[s] = r < args.nr ? args.doff[(size_t(lg) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
+        offs[s] = r < args.nr ? args.doff[(size_t(lev) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
     }
     __syncthreads();
 
@@ -787,10 +807,10 @@ cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_star
 }
 
 cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32_t *triples, int64_t ntriples,
-                        double *raw, cudaStream_t s)
+                        const GridArg &grids, double *raw, cudaStream_t s)
 {
     if (ntriples == 0) return cudaSuccess;
-    k_ntri<<<unsigned(ntriples), 256, 0, s>>>(ifields, ioff, triples, raw);
+    k_ntri<<<unsigned(ntriples), 256, 0, s>>>(ifields, ioff, triples, grids, raw);
     return cudaGetLastError();
 }
 
@@ -802,12 +822,12 @@ cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cuda
 }
 
 // explicit instantiations
-template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const float2 *, int, cudaStream_t);
-template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const double2 *, int, cudaStream_t);
-template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const float2 *, int, cudaStream_t);
-template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const double2 *, int, cudaStream_t);
-template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const float2 *, int, cudaStream_t);
-template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const double2 *, int, cudaStream_t);
+template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const Twiddles<float2> &, cudaStream_t);
+template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const Twiddles<double2> &, cudaStream_t);
+template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const Twiddles<float2> &, cudaStream_t);
+template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, cudaStream_t);
+template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, cudaStream_t);
+template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, cudaStream_t);
 template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, bool, cudaStream_t);
 template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, bool, cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, cudaStream_t);

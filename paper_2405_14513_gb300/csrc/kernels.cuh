@@ -21,6 +21,20 @@ struct RingArg {
     int maxc[kMaxRings];
 };
 
+// Twiddle tables of the transforms: tw2[k] = exp(-2 pi i k / 2^lg2) for
+// lengths 2^q <= 2^lg2 and tw3[k] = exp(-2 pi i k / (3 x 2^lg3)) for lengths
+// 3 x 2^q <= 3 x 2^lg3 (tw3 may be null when no such length is used).
+template <typename C> struct Twiddles {
+    const C *tw2;
+    const C *tw3;
+    int lg2, lg3;
+};
+
+// Side lengths of the plan's reduction grids, by level index.
+struct GridArg {
+    int M[kMaxLevels];
+};
+
 // Step-I job: one (plane, ring) field on one reduction grid.
 struct Job {
     int32_t n, r;
@@ -45,7 +59,7 @@ struct StepIIArgs {
 // frequencies [0, nkeep) written transposed as out[k][row].
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s);
 
 // Batched row transforms written transposed: in[b][nrow][M] -> out[b][M][nrow]
 // (out at out_off[b] when out_off is not null, else b * M * nrow), times
@@ -53,7 +67,7 @@ cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const typename Cx<R>::T *tw, int lg_tw, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s);
 
 // Step I, first pass: ring r of plane n of Delta (planes [nz+1][ng][ng]),
 // folded onto the M x M grid, transformed along u_y, written transposed to
@@ -61,7 +75,7 @@ cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *ou
 template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings,
                                const Job *jobs, int64_t njobs, int M, bool unit,
-                               typename Cx<R>::T *gt, const typename Cx<R>::T *tw, int lg_tw,
+                               typename Cx<R>::T *gt, const Twiddles<typename Cx<R>::T> &tw,
                                cudaStream_t s);
 
 // Step II: partial triple sums of every unit, one block per unit, one launch
@@ -88,8 +102,9 @@ cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_star
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);
 
 // N_tri of unordered ring triples from the unit fields (Eq. Ntri2), FP64.
+// triples[4 t .. 4 t + 3] = (r1, r2, r3, level index into grids.M).
 cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32_t *triples,
-                        int64_t ntriples, double *raw, cudaStream_t s);
+                        int64_t ntriples, const GridArg &grids, double *raw, cudaStream_t s);
 
 // Sizes of dynamic shared memory (bytes) of the transform kernels.
 size_t fft_rows_per_block(int M, size_t elem);

@@ -45,17 +45,21 @@ bool build_rings(int ng, Rings &R)
         }
     for (int q = 0; q < R.nr; ++q)
         R.kperp[q] = R.count[q] > 0 ? sum[q] / double(R.count[q]) : 0.5 * double(R.e3[q] + R.e3[q + 1]) / 3.0;
+    // reduction grids: 2^k and 3 x 2^k from 8 to N_g, ascending
+    R.ngrid = 0;
+    for (int m = 8; m <= ng; m *= 2) {
+        R.grid[R.ngrid++] = m;
+        if (3 * m / 2 <= ng) R.grid[R.ngrid++] = 3 * m / 2;
+    }
     return true;
 }
 
-int triple_log2m(const Rings &R, int r1, int r2, int r3)
+int triple_level(const Rings &R, int r1, int r2, int r3)
 {
-    int need = R.maxc[r1] + R.maxc[r2] + R.maxc[r3] + 1;
-    int lg = kMinLog2M;
-    while ((1 << lg) < need) ++lg;
-    int lgmax = 0;
-    while ((1 << lgmax) < R.ng) ++lgmax;
-    return std::min(lg, lgmax);
+    const int need = R.maxc[r1] + R.maxc[r2] + R.maxc[r3] + 1;
+    for (int l = 0; l < R.ngrid; ++l)
+        if (R.grid[l] >= need) return l;
+    return R.ngrid - 1;
 }
 
 namespace {
@@ -114,7 +118,7 @@ bool combo_geometry(const HostPlan &P, double kp1, double kp2, double kp3, int n
 }
 
 struct Acc {            // one accepted combination of a pair
-    uint8_t r1, r2, r3, lg;
+    uint8_t r1, r2, r3, lev;
     Geo g;
 };
 
@@ -144,7 +148,7 @@ void enumerate_pair(const HostPlan &P, int n1, int n2, PairOut &out)
                 Geo g;
                 if (!combo_geometry(P, R.kperp[r1], R.kperp[r2], R.kperp[r3], n1, n2, n3, &g)) continue;
                 out.acc.push_back(Acc{uint8_t(r1), uint8_t(r2), uint8_t(r3),
-                                      uint8_t(triple_log2m(R, r1, r2, r3)), g});
+                                      uint8_t(triple_level(R, r1, r2, r3)), g});
             }
         }
     }
@@ -168,7 +172,7 @@ int cover_windows(const uint8_t *cov, int ncov, uint8_t *w0)
 // 16 rows whose r3 runs need at most 8 windows; then units of 16, 8 or 4
 // tiles (one per warp) with the rings they stage.
 template <typename UsedFn>
-std::string build_mtiles(HostPlan &P, const Group &G, const Row *rw, const std::vector<int> &order, int lg,
+std::string build_mtiles(HostPlan &P, const Group &G, const Row *rw, const std::vector<int> &order, int lv,
                          int n1, int n2, int n3, std::vector<Unit> &unit_tmpl, UsedFn &&U_)
 {
     const int nr = P.rings.nr;
@@ -242,7 +246,7 @@ std::string build_mtiles(HostPlan &P, const Group &G, const Row *rw, const std::
         }
         const int nsabs[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
         for (int q = 0; q < 3; ++q)
-            for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lg, nsabs[q], r) = 1;
+            for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lv, nsabs[q], r) = 1;
         U.group = int32_t(P.groups.size());
         unit_tmpl.push_back(U);
         u0 = u1;
@@ -282,10 +286,9 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     }
 
     // used[l][n][r]: D fields to store
-    const int lgmax = [&] { int l = 0; while ((1 << l) < R.ng) ++l; return l; }();
     std::vector<uint8_t> used(size_t(kMaxLevels) * (nz + 1) * kMaxRings, 0);
-    auto U_ = [&](int lg, int n, int r) -> uint8_t & {
-        return used[(size_t(lg) * (nz + 1) + n) * kMaxRings + r];
+    auto U_ = [&](int lv, int n, int r) -> uint8_t & {
+        return used[(size_t(lv) * (nz + 1) + n) * kMaxRings + r];
     };
 
     P.groups.clear();
@@ -308,10 +311,11 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
         if (po.acc.empty()) continue;
         P.n_pairs++;
         const int n1 = po.n1, n2 = po.n2, n3 = -(n1 + n2);
-        for (int lg = kMinLog2M; lg <= lgmax; ++lg) {
+        for (int lv = 0; lv < R.ngrid; ++lv) {
             Group G{};
             G.n1 = n1; G.n2 = n2; G.n3 = n3;
-            G.log2m = lg;
+            G.lev = lv;
+            G.M = R.grid[lv];
             G.row0 = int32_t(P.rows.size());
             G.c0 = cidx;
             G.self_conj = (n1 == 0 && n2 == 0) ? 1 : 0;
@@ -320,12 +324,12 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             int last_r1 = -1, last_r2 = -1;
             size_t i = 0;
             while (i < po.acc.size()) {
-                if (po.acc[i].lg != lg) { ++i; continue; }
+                if (po.acc[i].lev != lv) { ++i; continue; }
                 // a run of consecutive r3 with the same (r1, r2) on this grid
                 const Acc &a = po.acc[i];
                 size_t j = i + 1;
                 int r3 = a.r3;
-                while (j < po.acc.size() && po.acc[j].lg == lg && po.acc[j].r1 == a.r1 &&
+                while (j < po.acc.size() && po.acc[j].lev == lv && po.acc[j].r1 == a.r1 &&
                        po.acc[j].r2 == a.r2 && po.acc[j].r3 == r3 + 1 && (j - i) < size_t(255)) {
                     ++j;
                     ++r3;
@@ -352,7 +356,7 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             if (ncombo == 0) continue;
             G.nrow = int32_t(P.rows.size()) - G.row0;
             G.ncombo = ncombo;
-            const int64_t M2 = int64_t(1) << (2 * lg);
+            const int64_t M2 = int64_t(G.M) * G.M;
             G.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
             P.triple_products += double(ncombo) * double(M2);
             P.pair_products += double(nrowpair) * double(M2);
@@ -386,7 +390,7 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                 }
             }
             if (P.tensor) {
-                std::string e = build_mtiles(P, G, rw, order, lg, n1, n2, n3, unit_tmpl, U_);
+                std::string e = build_mtiles(P, G, rw, order, lv, n1, n2, n3, unit_tmpl, U_);
                 if (!e.empty()) return e;
                 P.groups.push_back(G);
                 group_unit0.push_back(int32_t(unit_tmpl.size()));
@@ -445,7 +449,7 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                 }
                 const int nsabs[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
                 for (int q = 0; q < 3; ++q)
-                    for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lg, nsabs[q], r) = 1;
+                    for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lv, nsabs[q], r) = 1;
                 U.group = int32_t(P.groups.size());
                 unit_tmpl.push_back(U);
                 u0 = u1;
@@ -463,15 +467,16 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     P.levels.clear();
     int64_t cursor = 0;
     P.gt_elems = 0;
-    for (int lg = kMinLog2M; lg <= lgmax; ++lg) {
+    for (int lv = 0; lv < R.ngrid; ++lv) {
         Level L;
-        L.log2m = lg;
+        L.lev = lv;
+        L.M = R.grid[lv];
         L.dstore_off = cursor;
-        const int64_t M2 = int64_t(1) << (2 * lg);
+        const int64_t M2 = int64_t(L.M) * L.M;
         for (int n = 0; n <= nz; ++n)
             for (int r = 0; r < nr; ++r)
-                if (U_(lg, n, r)) {
-                    P.doff[(size_t(lg) * (nz + 1) + n) * kMaxRings + r] = cursor;
+                if (U_(lv, n, r)) {
+                    P.doff[(size_t(lv) * (nz + 1) + n) * kMaxRings + r] = cursor;
                     cursor += M2;
                     L.njobs++;
                 }
@@ -496,20 +501,20 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     auto blk = [&](const Group &G) { return std::make_pair((G.n1) / 8, (G.n2 + nz) / 8); };
     std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) {
         const Group &A = P.groups[a], &B = P.groups[b];
-        if (A.log2m != B.log2m) return A.log2m > B.log2m;
+        if (A.lev != B.lev) return A.lev > B.lev;
         return blk(A) < blk(B);
     });
     // units grouped by block class; within a class: grid, x chunk, pair block
     for (int cls = 2; cls <= 4; ++cls) {
         P.class_begin[cls] = int64_t(P.units.size());
-        for (int lg = lgmax; lg >= kMinLog2M; --lg) {
+        for (int lv = R.ngrid - 1; lv >= 0; --lv) {
             int maxchunk = 0;
             for (auto &G : P.groups)
-                if (G.log2m == lg) maxchunk = std::max(maxchunk, G.nchunk);
+                if (G.lev == lv) maxchunk = std::max(maxchunk, G.nchunk);
             for (int c = 0; c < maxchunk; ++c)
                 for (int32_t g : gorder) {
                     const Group &G = P.groups[g];
-                    if (G.log2m != lg || c >= G.nchunk) continue;
+                    if (G.lev != lv || c >= G.nchunk) continue;
                     for (int32_t u = group_unit0[g]; u < group_unit0[g + 1]; ++u) {
                         if (unit_tmpl[u].cls != cls) continue;
                         Unit U = unit_tmpl[u];

@@ -12,8 +12,7 @@
 namespace bisp {
 
 constexpr int kMaxRings = 64;     // N_r for N_g <= 1024 is 52
-constexpr int kMaxLevels = 11;    // reduction grids M = 2^3 .. 2^10
-constexpr int kMinLog2M = 3;      // smallest reduction grid, 8 x 8
+constexpr int kMaxLevels = 24;    // reduction grids: 2^k and 3 x 2^k from 8 to N_g
 constexpr int kTileRows = 8;      // rows (r1, r2) of a Step-II register tile
 constexpr int kTileCols = 8;      // consecutive r3 of a Step-II register tile
 
@@ -28,6 +27,8 @@ struct Rings {
     double kperp[kMaxRings] = {};      // mode-averaged |u|, grid units
     int64_t count[kMaxRings] = {};
     int maxc[kMaxRings] = {};          // largest |u_x| of a member (= largest |u_y|)
+    int ngrid = 0;                     // reduction grids, ascending: M = 2^k and 3 x 2^k,
+    int grid[kMaxLevels] = {};         // 8 <= M <= N_g
 };
 
 // Plane pair (n1, n2, n3 = -n1 - n2) on one reduction grid M: the set of
@@ -35,13 +36,13 @@ struct Rings {
 // are ordered by (r1, r2, r3).
 struct Group {
     int32_t n1, n2, n3;        // signed planes
-    int32_t log2m;             // reduction grid M = 2^log2m
+    int32_t lev;               // reduction grid index (Rings::grid)
+    int32_t M;                 // reduction grid side
     int32_t row0, nrow;        // rows of this group
-    int64_t c0;                // index of the first combination (S order)
     int32_t ncombo;
+    int64_t c0;                // index of the first combination (S order)
     int32_t nchunk;            // x chunks of the M^2 grid
     int32_t self_conj;         // 1 for n1 = n2 = 0 (counted once), else 0
-    int32_t pad;
     int64_t part0;             // partial sums [nchunk][ncombo] start here
 };
 
@@ -117,7 +118,8 @@ struct Record {
 };
 
 struct Level {
-    int log2m = 0;
+    int lev = 0;               // index into Rings::grid
+    int M = 0;                 // grid side
     int64_t njobs = 0;         // stored (plane, ring) fields on this grid
     int64_t dstore_off = 0;    // first element of this grid in the D store
 };
@@ -170,11 +172,11 @@ struct HostPlan {
 // Build the ring table; returns false for an unsupported N_g.
 bool build_rings(int ng, Rings &R);
 
-// Reduction grid of a ring triple: the smallest power of two M >= 8 with
-// M > maxc1 + maxc2 + maxc3, capped at N_g.  On that grid no non-zero sum
-// u + v + w of members aliases to zero, so the triple sum over x on the
-// M x M grid is exactly (M/N_g)^2 times the sum on the N_g x N_g grid.
-int triple_log2m(const Rings &R, int r1, int r2, int r3);
+// Reduction grid of a ring triple: the index of the smallest grid M with
+// M > maxc1 + maxc2 + maxc3 (the largest, N_g, if none).  On that grid no
+// non-zero sum u + v + w of members aliases to zero, so the triple sum over
+// the M x M grid is exactly (M/N_g)^2 times the sum on the N_g x N_g grid.
+int triple_level(const Rings &R, int r1, int r2, int r3);
 
 // Enumerate the accepted combinations of one half of the plane pairs and
 // fill groups, rows, tiles, units, records and the D-store layout.

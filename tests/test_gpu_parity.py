@@ -94,10 +94,10 @@ def test_step1_dfields_on_every_grid(c64):
                 continue
             seen.add(key)
             got = c64.plan.dfield(c64.ws, M, abs(int(n)), int(r))
-            full = O.dfield(c64.field64, c64.L, int(r), abs(int(n)))
-            step = c64.ng // M
-            want = full[::step, ::step]
+            want = O.dfield_at(c64.field64, c64.L, int(r), abs(int(n)), M)
             assert np.abs(got - want).max() < 2e-6 * max(np.abs(want).max(), 1e-30), key
+    grids = {int(M) for M, _, _ in seen}
+    assert any(M % 3 == 0 for M in grids) and any(M % 3 for M in grids), grids
 
 
 def test_combination_table_matches_oracle(c64):

@@ -63,6 +63,39 @@ def test_dfield_is_the_ring_sum_of_eq_iFT():
         assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max())
 
 
+def test_dfield_on_reduced_grids():
+    """D(r,n,x) at x = (N_g/M) y on M x M grids, M = 2^q or 3 x 2^q, against
+    the term-by-term ring sum; M = N_g reproduces the FFT-based field, and the
+    triple sum of Eq. fftbs on a grid with M > maxc1 + maxc2 + maxc3 times
+    (N_g/M)^2 equals the full-grid sum (no wrapped triangle u1+u2+u3 = M e)."""
+    ng, L = 16, 500.0
+    d = synth.make_field(ng, L, 5)
+    cube = np.fft.fftn(d) * (L ** 3 / ng ** 3)
+    cube[0, 0, 0] = 0
+    edges, kp, cnt = O.rings(ng)
+    for M in (8, 12, 16):
+        y = np.arange(M)
+        for r, n in [(0, 1), (1, 0), (2, -2)]:
+            got = O.dfield_at(d, L, r, n, M)
+            want = np.zeros((M, M), complex)
+            for i in range(-ng // 2, ng // 2):
+                for j in range(-ng // 2, ng // 2):
+                    if not (edges[r] <= math.hypot(i, j) < edges[r + 1]):
+                        continue
+                    want += cube[i % ng, j % ng, n % ng] * np.exp(-2j * np.pi * (i * y[:, None] + j * y[None, :]) / M)
+            assert np.abs(got - want).max() <= 1e-12 * max(1.0, np.abs(want).max()), (M, r, n)
+    assert np.abs(O.dfield_at(d, L, 2, 1, ng) - O.dfield(d, L, 2, 1)).max() <= 1e-12 * np.abs(O.dfield(d, L, 2, 1)).max()
+    # rings 1, 2, 2 reach |u_x|, |u_y| <= 1, 2, 2, so M = 8 and 12 hold the sum exactly
+    trip = [(1, 1), (2, 1), (2, -2)]
+    full = np.sum(np.prod([O.dfield(d, L, r, n) for r, n in trip], axis=0))
+    for M in (8, 12):
+        red = np.sum(np.prod([O.dfield_at(d, L, r, n, M) for r, n in trip], axis=0)) * (ng / M) ** 2
+        assert abs(red - full) <= 1e-10 * abs(full), M
+    # too small a grid wraps triangles in: the identity must fail at M = 4
+    red4 = np.sum(np.prod([O.dfield_at(d, L, r, n, 4) for r, n in trip], axis=0)) * (ng / 4) ** 2
+    assert abs(red4 - full) > 1e-6 * abs(full)
+
+
 # --------------------------------------------------------------------------
 # Rings (Sec. II)
 # --------------------------------------------------------------------------
