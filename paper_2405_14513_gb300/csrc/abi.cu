@@ -61,8 +61,12 @@ struct bisp_plan {
     std::vector<void *> owned;           // device allocations of the plan
     Group *d_groups = nullptr;
     Tile *d_tiles = nullptr;
-    MTile *d_mtiles = nullptr;
     Unit *d_units = nullptr;
+    TcTile *d_tc_tiles = nullptr;        // tcgen05 Step II (MIXED_TC)
+    TcRow *d_tc_rows = nullptr;
+    int32_t *d_tc_slots = nullptr;
+    TcUnit *d_tc_units = nullptr;
+    int *d_status = nullptr;             // set by a kernel whose bounded wait ran out
     int64_t *d_doff = nullptr;
     Record *d_rec = nullptr;
     int64_t *d_bin_start = nullptr;
@@ -352,8 +356,12 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
 
     st = upload(p, &p->d_groups, P.groups, s);
     if (!st) st = upload(p, &p->d_tiles, P.tiles, s);
-    if (!st) st = upload(p, &p->d_mtiles, P.mtiles, s);
     if (!st) st = upload(p, &p->d_units, P.units, s);
+    if (!st) st = upload(p, &p->d_tc_tiles, P.tc_tiles, s);
+    if (!st) st = upload(p, &p->d_tc_rows, P.tc_rows, s);
+    if (!st) st = upload(p, &p->d_tc_slots, P.tc_slots, s);
+    if (!st) st = upload(p, &p->d_tc_units, P.tc_units, s);
+    if (!st) st = upload(p, &p->d_status, std::vector<int>(1, 0), s);
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
     if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
@@ -415,6 +423,18 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     return BISP_OK;
 }
 
+// Step-II launches of one estimate (one per non-empty block class)
+int step2_launches(const HostPlan &P)
+{
+    int n = 0;
+    if (P.tensor) {
+        for (int c = 0; c < kTcClasses; ++c) n += P.tc_class_begin[c + 1] > P.tc_class_begin[c];
+    } else {
+        for (int c = 2; c <= 4; ++c) n += P.class_begin[c + 1] > P.class_begin[c];
+    }
+    return n;
+}
+
 template <typename R, typename A, typename S, typename W>
 int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, double *B, cudaStream_t s)
 {
@@ -432,7 +452,9 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
     const int64_t ng2 = int64_t(ng) * ng;
     const R scale = R(P.volume / (double(ng2) * ng));
-    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_mtiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
+    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
+    TcArgs atc{p->d_tc_tiles, p->d_tc_rows, p->d_tc_slots, p->d_tc_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk,
+               part, p->d_status};
     for (int b = 0; b < batch; ++b) {
         const R *d = delta + int64_t(b) * ng2 * ng;
         {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
@@ -451,8 +473,16 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
             }
         }
         {   // Step II: triple sums (Eq. fftbs)
-            StageMark m(p, BISP_STAGE_STEP2, sizeof(R) == 8 ? 2 : 3, s);
-            CK(launch_step2<R>(a2, dstore, P.class_begin, P.tensor, s));
+            StageMark m(p, BISP_STAGE_STEP2, step2_launches(P), s);
+            if constexpr (sizeof(R) == 4) {
+                if (P.tensor) {
+                    CK(launch_step2_tc(atc, dstore, P.tc_class_begin, P.tc_class_slots, s));
+                } else {
+                    CK(launch_step2<R>(a2, dstore, P.class_begin, s));
+                }
+            } else {
+                CK(launch_step2<R>(a2, dstore, P.class_begin, s));
+            }
         }
         {
             StageMark m(p, BISP_STAGE_REDUCE, 1, s);
@@ -526,7 +556,7 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->n_bins = P.n_bins;
     info->n_combos = P.n_combos;
     info->n_pairs = P.n_pairs;
-    info->n_items = int64_t(P.units.size());
+    info->n_items = int64_t(P.tensor ? P.tc_units.size() : P.units.size());
     info->triple_products = P.triple_products;
     info->dstore_bytes = size_t(P.dstore_elems) * p->celem;
     info->workspace_bytes = p->ws_bytes;

@@ -550,176 +550,6 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------
-// Step II on the tensor cores (FP32 paths).  Same units and staging as
-// k_step2, but each warp takes a tile of 16 rows and up to 8 windows of 8
-// consecutive r3, and the sum over grid points runs as a real matrix product
-// on mma.sync m16n8k8 (TF32 inputs, FP32 accumulation):
-//   C[row][col] = sum_k A[row][k] B[k][col],  k = 4 c + p for the 4 grid
-//   points p of a step and c = 0 (real) / 1 (imaginary),
-//   A[row][(p,0)] = Re P, A[row][(p,1)] = -g3 Im P, P = D(r1,n1) D(r2,n2),
-//   B[(p,0)][col] = Re D(w0+col, n3), B[(p,1)][col] = Im D(w0+col, n3),
-// so that C = Re sum_x P D(r3, n3) with the sign factors of conjugated
-// planes.  With this k order lane (g, t) (g = lane/4, t = lane%4) owns grid
-// point t of each step: it forms P for rows g and g+8 once and loads one
-// complex D(r3) per window.  Each FP32 operand x is split x = hi + lo with
-// hi, lo in TF32 and the product taken as hi*hi' + hi*lo' + lo*hi' (the
-// lo*lo' term is below FP32 rounding), which keeps FP32 accuracy.  The MMA
-// accumulators are added into FP32 totals every 8 steps.
-__device__ __forceinline__ uint32_t to_tf32(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
-{
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-template <int NW>
-__global__ void __launch_bounds__(32 * NW, 16 / NW)
-k_step2_mma(StepIIArgs args, int64_t unit0, const float2 *__restrict__ dstore, int smem_bytes)
-{
-    using C = float2;
-    constexpr int NT = 32 * NW;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Unit U = args.units[unit0 + blockIdx.x];
-    const Group G = args.groups[U.group];
-    const int lev = G.lev;
-    const int64_t M2 = int64_t(G.M) * G.M;
-    const int64_t x0 = int64_t(U.chunk) * args.x_chunk;
-    const int64_t x1 = min(M2, x0 + args.x_chunk);
-    const int nq0 = U.rhi[0] - U.rlo[0] + 1, nq1 = U.rhi[1] - U.rlo[1] + 1, nq2 = U.rhi[2] - U.rlo[2] + 1;
-    const int ns = nq0 + nq1 + nq2;
-
-    int64_t *offs = reinterpret_cast<int64_t *>(smem_raw);
-    const size_t off = (size_t(ns) * sizeof(int64_t) + 127) & ~size_t(127);
-    C *buf = reinterpret_cast<C *>(smem_raw + off);
-    // grid points per stage (multiple of 32, at most 256); slot rows are
-    // padded by 4 points so that the 8 rows a warp reads fall in different banks
-    int TX = int((size_t(smem_bytes) - off) / (2 * size_t(ns) * sizeof(C))) - 4;
-    TX = min(256, TX & ~31);
-    const int SP = TX + 4;
-    const size_t stage_elems = size_t(ns) * SP;
-
-    for (int s = threadIdx.x; s < ns; s += NT) {
-        const int q = s < nq0 ? 0 : (s < nq0 + nq1 ? 1 : 2);
-        const int r = U.rlo[q] + s - (q == 0 ? 0 : (q == 1 ? nq0 : nq0 + nq1));
-        const int n = q == 0 ? G.n1 : (q == 1 ? G.n2 : G.n3);
-        offs[s] = r < args.nr ? args.doff[(size_t(lev) * args.nz1 + (n < 0 ? -n : n)) * kMaxRings + r] : -1;
-    }
-    __syncthreads();
-
-    const float g1 = G.n1 < 0 ? -1.f : 1.f, g2 = G.n2 < 0 ? -1.f : 1.f, g3 = G.n3 < 0 ? -1.f : 1.f;
-    const float k12 = -g1 * g2, k32 = g3 * g2, k31 = g3 * g1;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const bool active = warp < U.nt;
-    const MTile *T = args.mtiles + U.t0 + (active ? warp : 0);
-    const int nwin = active ? T->nwin : 0;
-    int o1a = 0, o2a = 0, o1b = 0, o2b = 0;
-    int o3[kMWins];
-    if (active) {
-        o1a = T->row[g].s1 * SP + t;
-        o2a = T->row[g].s2 * SP + t;
-        o1b = T->row[g + 8].s1 * SP + t;
-        o2b = T->row[g + 8].s2 * SP + t;
-    }
-#pragma unroll
-    for (int j = 0; j < kMWins; ++j) o3[j] = active ? (T->s3[j] + g) * SP + t : 0;
-    float acc[kMWins][4], tot[kMWins][4];
-#pragma unroll
-    for (int j = 0; j < kMWins; ++j)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[j][e] = tot[j][e] = 0.f;
-
-    const int nstage = int((x1 - x0 + TX - 1) / TX);
-    auto issue = [&](int st) {
-        C *dst = buf + size_t(st & 1) * stage_elems;
-        const int64_t xs = x0 + int64_t(st) * TX;
-        const int nx = int(min(int64_t(TX), x1 - xs));
-        const int per = TX / 2;                       // 16-byte pieces per slot row
-        for (int k = threadIdx.x; k < ns * per; k += NT) {
-            const int s = k / per, c = (k - s * per) * 2;
-            C *d = dst + size_t(s) * SP + c;
-            if (offs[s] >= 0 && c < nx) cp_async16(d, dstore + offs[s] + xs + c);
-            else *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-        asm volatile("cp.async.commit_group;\n" ::);
-    };
-    issue(0);
-    for (int st = 0; st < nstage; ++st) {
-        if (st + 1 < nstage) {
-            issue(st + 1);
-            asm volatile("cp.async.wait_group 1;\n" ::);
-        } else {
-            asm volatile("cp.async.wait_group 0;\n" ::);
-        }
-        __syncthreads();
-        const C *b = buf + size_t(st & 1) * stage_elems;
-        const int nx = int(min(int64_t(TX), x1 - (x0 + int64_t(st) * TX)));
-        if (active) {
-            for (int xb = 0; xb < nx; xb += 32) {
-#pragma unroll 2
-                for (int xs = 0; xs < 32; xs += 4) {
-                    const int x = xb + xs;
-                    const C u0 = b[o1a + x], v0 = b[o2a + x], u1 = b[o1b + x], v1 = b[o2b + x];
-                    float av[4];
-                    av[0] = fmaf(u0.x, v0.x, k12 * (u0.y * v0.y));
-                    av[1] = fmaf(u1.x, v1.x, k12 * (u1.y * v1.y));
-                    av[2] = -fmaf(k32 * u0.x, v0.y, k31 * (u0.y * v0.x));
-                    av[3] = -fmaf(k32 * u1.x, v1.y, k31 * (u1.y * v1.x));
-                    uint32_t ah[4], al[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        ah[e] = to_tf32(av[e]);
-                        al[e] = to_tf32(av[e] - __uint_as_float(ah[e]));
-                    }
-#pragma unroll
-                    for (int j = 0; j < kMWins; ++j) {
-                        if (j < nwin) {
-                            const C d = b[o3[j] + x];
-                            const uint32_t bh0 = to_tf32(d.x), bh1 = to_tf32(d.y);
-                            const uint32_t bl0 = to_tf32(d.x - __uint_as_float(bh0));
-                            const uint32_t bl1 = to_tf32(d.y - __uint_as_float(bh1));
-                            mma_tf32(acc[j], ah, bh0, bh1);
-                            mma_tf32(acc[j], ah, bl0, bl1);
-                            mma_tf32(acc[j], al, bh0, bh1);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < kMWins; ++j)
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        tot[j][e] += acc[j][e];
-                        acc[j][e] = 0.f;
-                    }
-            }
-        }
-        __syncthreads();
-    }
-    if (!active) return;
-    double *dst = args.partials + G.part0 + int64_t(U.chunk) * G.ncombo;
-#pragma unroll
-    for (int j = 0; j < kMWins; ++j) {
-        if (j >= nwin) break;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int row = g + 8 * (e >> 1);
-            const MRow R = T->row[row];
-            const int r3 = T->w0[j] + 2 * t + (e & 1);
-            if (R.n > 0 && r3 >= R.r3a && r3 < R.r3a + R.n) dst[R.coff + (r3 - R.r3a)] = double(tot[j][e]);
-        }
-    }
-}
-
 template <typename R, int NW>
 cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t u0, int64_t n,
                                size_t smem, cudaStream_t s)
@@ -731,42 +561,19 @@ cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dst
     return cudaGetLastError();
 }
 
-template <int NW>
-cudaError_t launch_step2_mma_class(const StepIIArgs &a, const float2 *dstore, int64_t u0, int64_t n, size_t smem,
-                                   cudaStream_t s)
-{
-    if (n == 0) return cudaSuccess;
-    cudaError_t e = set_smem(k_step2_mma<NW>, smem);
-    if (e != cudaSuccess) return e;
-    k_step2_mma<NW><<<unsigned(n), 32 * NW, smem, s>>>(a, u0, dstore, int(smem));
-    return cudaGetLastError();
-}
-
 template <typename R>
 cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
-                         bool tensor, cudaStream_t s)
+                         cudaStream_t s)
 {
     if constexpr (sizeof(R) == 4) {
-        if (!tensor) {
-            cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                                     kStep2ClassSmem[2], s);
-            if (e == cudaSuccess)
-                e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                             kStep2ClassSmem[3], s);
-            if (e == cudaSuccess)
-                e = launch_step2_class<R, 16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
-                                              kStep2ClassSmem[4], s);
-            return e;
-        }
-        // tensor-core tiles
-        cudaError_t e = launch_step2_mma_class<4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                                  kStep2ClassSmem[2], s);
+        cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
+                                                 kStep2ClassSmem[2], s);
         if (e == cudaSuccess)
-            e = launch_step2_mma_class<8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                          kStep2ClassSmem[3], s);
+            e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
+                                         kStep2ClassSmem[3], s);
         if (e == cudaSuccess)
-            e = launch_step2_mma_class<16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
-                                           kStep2ClassSmem[4], s);
+            e = launch_step2_class<R, 16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
+                                          kStep2ClassSmem[4], s);
         return e;
     }
     // FP64: register tiles, blocks of at most 8 warps (register file)
@@ -828,8 +635,8 @@ template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int
 template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, cudaStream_t);
 template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, cudaStream_t);
 template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, cudaStream_t);
-template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, bool, cudaStream_t);
-template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, bool, cudaStream_t);
+template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, cudaStream_t);
+template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
 template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
 template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, cudaStream_t);

@@ -43,8 +43,7 @@ struct Job {
 
 struct StepIIArgs {
     const Group *groups;
-    const Tile *tiles;       // FP64 path
-    const MTile *mtiles;     // FP32 paths (tensor cores)
+    const Tile *tiles;
     const Unit *units;
     const int64_t *doff;     // [kMaxLevels][nz+1][kMaxRings]
     int nz1;                 // planes stored: 0 .. nz1 - 1
@@ -81,10 +80,31 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
 // Step II: partial triple sums of every unit, one block per unit, one launch
 // per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
 // 2^c warps with kStep2ClassSmem[c] bytes of shared memory).
-// tensor: the plan built tensor-core tiles (FP32 paths only).
 template <typename R>
 cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
-                         bool tensor, cudaStream_t s);
+                         cudaStream_t s);
+
+// Step II on tcgen05 (FP32 fields; step2_tc.cu).
+struct TcArgs {
+    const TcTile *tiles;
+    const TcRow *rows;
+    const int32_t *slots;
+    const TcUnit *units;
+    const int64_t *doff;     // [kMaxLevels][nz+1][kMaxRings]
+    int nz1, nr;
+    int64_t x_chunk;
+    double *partials;
+    int *status;             // set to 1 by a block whose tensor-core wait ran out
+};
+
+// Dynamic shared memory of a tcgen05 Step-II block of NC = 16 (cls + 1)
+// columns staging up to nslot D1 / D2 fields.
+size_t step2_tc_smem(int cls, int nslot);
+
+// One launch per column class: units [class_begin[c], class_begin[c+1]),
+// one 128-thread block per unit.
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin,
+                            const int *class_slots, cudaStream_t s);
 
 // S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
 template <typename A>

@@ -154,103 +154,140 @@ void enumerate_pair(const HostPlan &P, int n1, int n2, PairOut &out)
     }
 }
 
-// Windows of 8 consecutive r3 covering the set cov (greedy from the lowest);
-// returns their count and writes their first r3 to w0 (when not null).
-int cover_windows(const uint8_t *cov, int ncov, uint8_t *w0)
-{
-    int n = 0;
-    for (int c = 0; c < ncov;) {
-        if (!cov[c]) { ++c; continue; }
-        if (w0 && n < kMWins) w0[n] = uint8_t(c);
-        ++n;
-        c += kTileCols;
-    }
-    return n;
-}
-
-// Tensor-core tiles of one group: rows in the given order, blocks of up to
-// 16 rows whose r3 runs need at most 8 windows; then units of 16, 8 or 4
-// tiles (one per warp) with the rings they stage.
+// tcgen05 tiles (see TcTile): the groups of each (grid, |n3|) in order of
+// (sign of n3, n1), their rows by the centre of their r3 run, cut greedily
+// into tiles of at most 128 rows, a window of at most 64 r3 and at most
+// kTcMaxSlots staged D1 / D2 fields; then units (tile, x chunk) by class.
+// Requires the groups' partial-sum layout.  Marks the fields the tiles read.
 template <typename UsedFn>
-std::string build_mtiles(HostPlan &P, const Group &G, const Row *rw, const std::vector<int> &order, int lv,
-                         int n1, int n2, int n3, std::vector<Unit> &unit_tmpl, UsedFn &&U_)
+std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
 {
-    const int nr = P.rings.nr;
-    struct Blk { int rows[kMRows]; int nr; uint8_t w0[kMWins]; int nwin; };
-    std::vector<Blk> blks;
-    const int ncov = kMaxRings + kTileCols;
-    for (int b = 0; b < G.nrow;) {
-        Blk k{};
-        std::vector<uint8_t> cov(ncov, 0);
-        while (b < G.nrow && k.nr < kMRows) {
-            std::vector<uint8_t> c2 = cov;
-            const Row &r = rw[order[b]];
-            for (int c = 0; c < r.n; ++c) c2[r.r3a + c] = 1;
-            if (k.nr > 0 && cover_windows(c2.data(), ncov, nullptr) > kMWins) break;
-            cov.swap(c2);
-            k.rows[k.nr++] = order[b++];
-        }
-        k.nwin = cover_windows(cov.data(), ncov, k.w0);
-        if (k.nwin > kMWins) return "a row needs more than 8 windows";
-        blks.push_back(k);
+    const Rings &R = P.rings;
+    const int nz = R.nz;
+    P.tc_tiles.clear();
+    P.tc_rows.clear();
+    P.tc_slots.clear();
+    P.tc_units.clear();
+    P.tc_mma_products = 0;
+    for (int c = 0; c < kTcClasses; ++c) P.tc_class_slots[c] = 0;
+    std::vector<std::vector<int32_t>> pool(size_t(R.ngrid) * (nz + 1));
+    for (size_t g = 0; g < P.groups.size(); ++g) {
+        const Group &G = P.groups[g];
+        pool[size_t(G.lev) * (nz + 1) + (G.n3 < 0 ? -G.n3 : G.n3)].push_back(int32_t(g));
     }
-    size_t u0 = 0;
-    while (u0 < blks.size()) {
-        const size_t rem = blks.size() - u0;
-        int cls = rem > 8 ? 4 : (rem > 4 ? 3 : 2);
-        if (cls > P.max_cls) cls = P.max_cls;
-        const size_t take = std::min(rem, size_t(1) << cls);
-        const size_t u1 = u0 + take;
-        Unit U{};
-        U.t0 = int32_t(P.mtiles.size());
-        U.nt = int32_t(take);
-        int lo[3] = {nr, nr, kMaxRings}, hi[3] = {-1, -1, -1};
-        for (size_t t = u0; t < u1; ++t) {
-            const Blk &k = blks[t];
-            for (int q = 0; q < k.nr; ++q) {
-                const Row &r = rw[k.rows[q]];
-                lo[0] = std::min<int>(lo[0], r.r1); hi[0] = std::max<int>(hi[0], r.r1);
-                lo[1] = std::min<int>(lo[1], r.r2); hi[1] = std::max<int>(hi[1], r.r2);
-            }
-            for (int j = 0; j < k.nwin; ++j) {
-                lo[2] = std::min<int>(lo[2], k.w0[j]);
-                hi[2] = std::max<int>(hi[2], k.w0[j] + kTileCols - 1);
+    struct Cur {
+        std::vector<std::pair<int32_t, int32_t>> rows;   // (group, row index in P.rows)
+        std::vector<int32_t> slots;
+        int lo = 1 << 30, hi = -1;
+    } cur;
+    int cur_lev = 0, cur_n3 = 0;
+    auto slot_of = [&](std::vector<int32_t> &sl, int32_t key) {
+        for (size_t i = 0; i < sl.size(); ++i)
+            if (sl[i] == key) return int(i);
+        return -1;
+    };
+    auto close = [&]() -> std::string {
+        if (cur.rows.empty()) return "";
+        TcTile T{};
+        T.lev = cur_lev;
+        T.M = R.grid[cur_lev];
+        T.row0 = int32_t(P.tc_rows.size());
+        T.nrow = int32_t(cur.rows.size());
+        T.slot0 = int32_t(P.tc_slots.size());
+        T.nslot = int32_t(cur.slots.size());
+        T.n3abs = cur_n3;
+        T.r3lo = cur.lo;
+        T.ncol = ((cur.hi - cur.lo + 1 + 15) / 16) * 16;
+        const int64_t M2 = int64_t(T.M) * T.M;
+        T.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
+        if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows) return "tcgen05 tile limits";
+        for (auto &gr : cur.rows) {
+            const Group &G = P.groups[gr.first];
+            const Row &rw = P.rows[gr.second];
+            TcRow t{};
+            t.p0 = G.part0 + rw.coff;
+            t.stride = G.ncombo;
+            const int a1 = G.n1 < 0 ? -G.n1 : G.n1, a2 = G.n2 < 0 ? -G.n2 : G.n2;
+            t.s1 = uint8_t(slot_of(cur.slots, (a1 << 8) | rw.r1));
+            t.s2 = uint8_t(slot_of(cur.slots, (a2 << 8) | rw.r2));
+            t.col0 = uint8_t(rw.r3a - cur.lo);
+            t.n = rw.n;
+            t.flags = uint8_t((G.n1 < 0 ? 1 : 0) | (G.n2 < 0 ? 2 : 0) | (G.n3 < 0 ? 4 : 0));
+            P.tc_rows.push_back(t);
+            U_(cur_lev, a1, rw.r1) = 1;
+            U_(cur_lev, a2, rw.r2) = 1;
+            for (int j = 0; j < rw.n; ++j) U_(cur_lev, cur_n3, rw.r3a + j) = 1;
+        }
+        P.tc_slots.insert(P.tc_slots.end(), cur.slots.begin(), cur.slots.end());
+        const int cls = T.ncol / 16 - 1;
+        P.tc_class_slots[cls] = std::max(P.tc_class_slots[cls], T.nslot);
+        P.tc_mma_products += double(kTcRows) * T.ncol * double(M2);
+        P.tc_tiles.push_back(T);
+        cur = Cur{};
+        return "";
+    };
+    for (int lv = 0; lv < R.ngrid; ++lv)
+        for (int n3 = 0; n3 <= nz; ++n3) {
+            std::vector<int32_t> &gl = pool[size_t(lv) * (nz + 1) + n3];
+            if (gl.empty()) continue;
+            std::stable_sort(gl.begin(), gl.end(), [&](int32_t a, int32_t b) {
+                const Group &A = P.groups[a], &B = P.groups[b];
+                if ((A.n3 < 0) != (B.n3 < 0)) return A.n3 >= 0;
+                return A.n1 < B.n1;
+            });
+            std::string e = close();
+            if (!e.empty()) return e;
+            cur_lev = lv;
+            cur_n3 = n3;
+            for (int32_t g : gl) {
+                const Group &G = P.groups[g];
+                std::vector<int32_t> order(G.nrow);
+                for (int q = 0; q < G.nrow; ++q) order[q] = G.row0 + q;
+                std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+                    const Row &X = P.rows[x], &Y = P.rows[y];
+                    const int cx = 2 * X.r3a + X.n, cy = 2 * Y.r3a + Y.n;
+                    return cx != cy ? cx < cy : X.r3a < Y.r3a;
+                });
+                const int a1 = G.n1 < 0 ? -G.n1 : G.n1, a2 = G.n2 < 0 ? -G.n2 : G.n2;
+                for (int32_t ri : order) {
+                    const Row &rw = P.rows[ri];
+                    if (rw.n > kTcMaxCols) return "a row's r3 run is longer than a tcgen05 window";
+                    const int k1 = (a1 << 8) | rw.r1, k2 = (a2 << 8) | rw.r2;
+                    if (!cur.rows.empty()) {
+                        const int lo = std::min(cur.lo, int(rw.r3a)), hi = std::max(cur.hi, rw.r3a + rw.n - 1);
+                        const int add = (slot_of(cur.slots, k1) < 0) + (k2 != k1 && slot_of(cur.slots, k2) < 0);
+                        if (int(cur.rows.size()) >= kTcRows || hi - lo + 1 > kTcMaxCols ||
+                            int(cur.slots.size()) + add > kTcMaxSlots) {
+                            e = close();
+                            if (!e.empty()) return e;
+                        }
+                    }
+                    if (slot_of(cur.slots, k1) < 0) cur.slots.push_back(k1);
+                    if (slot_of(cur.slots, k2) < 0) cur.slots.push_back(k2);
+                    cur.lo = std::min(cur.lo, int(rw.r3a));
+                    cur.hi = std::max(cur.hi, rw.r3a + rw.n - 1);
+                    cur.rows.emplace_back(g, ri);
+                }
             }
         }
-        for (int q = 0; q < 3; ++q) { U.rlo[q] = int16_t(lo[q]); U.rhi[q] = int16_t(hi[q]); }
-        const int nq0 = hi[0] - lo[0] + 1, nq1 = hi[1] - lo[1] + 1, nq2 = hi[2] - lo[2] + 1;
-        const int ns = nq0 + nq1 + nq2;
-        if (ns > 255) return "too many staged rings in a Step-II unit";
-        while (cls < P.max_cls && step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls]) ++cls;
-        if (step2_smem_need(ns, 64, P.celem) > kStep2ClassSmem[cls]) return "Step-II unit too large for shared memory";
-        U.cls = cls;
-        P.max_slots = std::max(P.max_slots, ns);
-        for (size_t t = u0; t < u1; ++t) {
-            const Blk &k = blks[t];
-            MTile T{};
-            for (int q = 0; q < kMRows; ++q) {
-                const Row &r = rw[k.rows[q < k.nr ? q : 0]];
-                T.row[q].s1 = uint8_t(r.r1 - lo[0]);
-                T.row[q].s2 = uint8_t(nq0 + r.r2 - lo[1]);
-                T.row[q].r3a = r.r3a;
-                T.row[q].n = q < k.nr ? r.n : 0;
-                T.row[q].coff = r.coff;
-            }
-            for (int j = 0; j < kMWins; ++j) {
-                const int w = j < k.nwin ? k.w0[j] : k.w0[0];
-                T.w0[j] = uint8_t(w);
-                T.s3[j] = uint8_t(nq0 + nq1 + w - lo[2]);
-            }
-            T.nwin = k.nwin;
-            P.mtiles.push_back(T);
+    std::string e = close();
+    if (!e.empty()) return e;
+    // units: class, then biggest grids first, x chunk, tile
+    for (int c = 0; c < kTcClasses; ++c) {
+        P.tc_class_begin[c] = int64_t(P.tc_units.size());
+        for (int lv = R.ngrid - 1; lv >= 0; --lv) {
+            int maxchunk = 0;
+            for (const auto &T : P.tc_tiles)
+                if (T.lev == lv && T.ncol / 16 - 1 == c) maxchunk = std::max(maxchunk, T.nchunk);
+            for (int ch = 0; ch < maxchunk; ++ch)
+                for (size_t t = 0; t < P.tc_tiles.size(); ++t) {
+                    const TcTile &T = P.tc_tiles[t];
+                    if (T.lev != lv || T.ncol / 16 - 1 != c || ch >= T.nchunk) continue;
+                    P.tc_units.push_back(TcUnit{int32_t(t), ch});
+                }
         }
-        const int nsabs[3] = {n1 < 0 ? -n1 : n1, n2 < 0 ? -n2 : n2, n3 < 0 ? -n3 : n3};
-        for (int q = 0; q < 3; ++q)
-            for (int r = lo[q]; r <= std::min(hi[q], nr - 1); ++r) U_(lv, nsabs[q], r) = 1;
-        U.group = int32_t(P.groups.size());
-        unit_tmpl.push_back(U);
-        u0 = u1;
     }
+    P.tc_class_begin[kTcClasses] = int64_t(P.tc_units.size());
     return "";
 }
 
@@ -294,7 +331,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     P.groups.clear();
     P.rows.clear();
     P.tiles.clear();
-    P.mtiles.clear();
     P.units.clear();
     P.records_s.clear();
     P.ntri_s.clear();
@@ -362,6 +398,11 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             P.pair_products += double(nrowpair) * double(M2);
             cidx += ncombo;
 
+            if (P.tensor) {             // tcgen05 tiles span groups: built after the loop
+                P.groups.push_back(G);
+                group_unit0.push_back(int32_t(unit_tmpl.size()));
+                continue;
+            }
             // register tiles: rows ordered by the centre of their r3 run,
             // blocks of kTileRows rows, each block cut into windows of
             // kTileCols consecutive r3 covering the union of its runs
@@ -388,13 +429,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                     raws.push_back(t);
                     for (int d = 0; d < kTileCols; ++d) cov[c + d] = 0;
                 }
-            }
-            if (P.tensor) {
-                std::string e = build_mtiles(P, G, rw, order, lv, n1, n2, n3, unit_tmpl, U_);
-                if (!e.empty()) return e;
-                P.groups.push_back(G);
-                group_unit0.push_back(int32_t(unit_tmpl.size()));
-                continue;
             }
             // units: runs of 16, 8 or 4 consecutive tiles (one per warp), each
             // staging the union of its tiles' rings
@@ -462,6 +496,18 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     P.n_combos = cidx;
     if (P.n_combos >= (int64_t(1) << 31) - 1) return "too many combinations for 32-bit indices";
 
+    // partial sums [group][x chunk][combination]
+    int64_t part = 0;
+    for (auto &G : P.groups) {
+        G.part0 = part;
+        part += int64_t(G.nchunk) * G.ncombo;
+    }
+    P.n_partials = part;
+    if (P.tensor) {
+        std::string e = build_tc(P, x_chunk, U_);
+        if (!e.empty()) return e;
+    }
+
     // D-store layout, grid by grid, plane by plane, ring by ring
     P.doff.assign(size_t(kMaxLevels) * (nz + 1) * kMaxRings, -1);
     P.levels.clear();
@@ -487,15 +533,10 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     }
     P.dstore_elems = cursor;
 
-    // partial-sum layout and Step-II units in launch order: biggest grids
+    // Step-II units in launch order: biggest grids
     // first, then by x chunk, then by blocks of 8 x 8 plane pairs, so that
     // blocks running together share planes (and their rings) in L2
-    int64_t part = 0;
-    for (auto &G : P.groups) {
-        G.part0 = part;
-        part += int64_t(G.nchunk) * G.ncombo;
-    }
-    P.n_partials = part;
+    if (P.tensor) return "";
     std::vector<int32_t> gorder(P.groups.size());
     for (size_t g = 0; g < gorder.size(); ++g) gorder[g] = int32_t(g);
     auto blk = [&](const Group &G) { return std::make_pair((G.n1) / 8, (G.n2 + nz) / 8); };

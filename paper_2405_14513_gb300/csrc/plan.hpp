@@ -67,24 +67,34 @@ struct Tile {
 };
 static_assert(sizeof(Tile) == 64, "Tile is copied in 16-byte pieces");
 
-// Tensor-core Step-II tile: up to 16 rows of one group times up to 8 windows
-// of 8 consecutive r3 (each placed where the rows need it).  Row i's
-// combinations are (r3a .. r3a + n - 1) -> coff .. coff + n - 1; padding rows
-// have n = 0.
-struct MRow {
-    uint8_t s1, s2, r3a, n;    // staged slots of D(r1, n1), D(r2, n2); r3 run
-    int32_t coff;
+// Tensor-core (tcgen05) Step II.  A tile is up to 128 rows (r1, r2) taken
+// from groups that share the reduction grid and |n3|, times a window of NC
+// consecutive r3 (r3lo .. r3lo + NC - 1) of plane |n3|; NC = 16, 32, 48 or
+// 64.  The pair products D1 D2 of the rows form the MMA's A operand (one row
+// per tensor-memory lane), the window's stored D3 fields its B operand.
+constexpr int kTcRows = 128;
+constexpr int kTcMaxCols = 64;
+constexpr int kTcMaxSlots = 160;      // distinct D1 / D2 fields staged by a tile
+constexpr int kTcClasses = 4;         // NC = 16 (class + 1)
+struct TcRow {
+    int64_t p0;                // partial sum of (x chunk 0, first combination of the run)
+    int32_t stride;            // partial sums of one x chunk of the row's group (its ncombo)
+    uint8_t s1, s2;            // staged slots of D(r1, |n1|) and D(r2, |n2|)
+    uint8_t col0, n;           // combinations r3 = r3lo + col0 .. r3lo + col0 + n - 1
+    uint8_t flags;             // bit 0: n1 < 0, bit 1: n2 < 0, bit 2: n3 < 0 (conjugated fields)
+    uint8_t pad[7];
 };
-constexpr int kMRows = 16;
-constexpr int kMWins = 8;
-struct MTile {
-    MRow row[kMRows];
-    uint8_t s3[kMWins];        // staged slot of the first r3 of each window
-    uint8_t w0[kMWins];        // first r3 of each window
-    int32_t nwin;
-    int32_t pad[3];
+static_assert(sizeof(TcRow) == 24, "TcRow layout");
+struct TcTile {
+    int32_t lev, M;            // reduction grid
+    int32_t row0, nrow;        // rows in tc_rows
+    int32_t slot0, nslot;      // staged D1 / D2 fields in tc_slots: (plane << 8) | ring
+    int32_t n3abs, r3lo;       // B window: rings r3lo .. r3lo + ncol - 1 of plane |n3|
+    int32_t ncol, nchunk;      // NC; x chunks of the M^2 grid
 };
-static_assert(sizeof(MTile) == 160, "MTile is copied in 16-byte pieces");
+struct TcUnit {
+    int32_t tile, chunk;
+};
 
 // One Step-II block: an x chunk of a group with up to 16 of its tiles (one
 // per warp), and the ring ranges it stages per plane (plane 3 may reach
@@ -140,8 +150,14 @@ struct HostPlan {
     std::vector<Group> groups;
     std::vector<Row> rows;
     std::vector<Tile> tiles;            // FP64 path: 8 x 8 register tiles
-    std::vector<MTile> mtiles;          // FP32 paths: 16-row tensor-core tiles
-    bool tensor = false;                // build mtiles (set before enumerate)
+    bool tensor = false;                // build tcgen05 tiles (set before enumerate)
+    std::vector<TcTile> tc_tiles;
+    std::vector<TcRow> tc_rows;
+    std::vector<int32_t> tc_slots;
+    std::vector<TcUnit> tc_units;       // by class (NC), then grid, x chunk, tile
+    int64_t tc_class_begin[kTcClasses + 1] = {};
+    int tc_class_slots[kTcClasses] = {};    // largest nslot of a tile of each class
+    double tc_mma_products = 0;         // sum over tiles of 128 NC M^2 (lane-column-points)
     std::vector<Unit> units;            // Step-II blocks in launch order
     int max_slots = 0;                  // largest staged ring count of a unit
     int max_cls = 4;                    // largest block class (set before enumerate)
