@@ -58,6 +58,7 @@ struct bisp_plan {
     HostPlan hp;
     int precision = BISP_PREC_MIXED;
     size_t celem = 8;                    // bytes of one complex field value
+    int64_t x_chunk = 0;                 // grid points of one Step-II unit
     std::vector<void *> owned;           // device allocations of the plan
     Group *d_groups = nullptr;
     Tile *d_tiles = nullptr;
@@ -350,7 +351,8 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     P.celem = p->celem;
     P.max_cls = desc->precision == BISP_PREC_FP64 ? 3 : 4;   // FP64 blocks have at most 8 warps
     P.tensor = desc->precision == BISP_PREC_MIXED_TC;       // Step II on tensor cores
-    std::string err = enumerate(P, kXChunk);
+    p->x_chunk = kXChunk;
+    std::string err = enumerate(P, p->x_chunk);
     if (!err.empty()) return fail(BISP_INTERNAL, err);
     sort_records(P);
 
@@ -452,8 +454,8 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
     const int64_t ng2 = int64_t(ng) * ng;
     const R scale = R(P.volume / (double(ng2) * ng));
-    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk, part};
-    TcArgs atc{p->d_tc_tiles, p->d_tc_rows, p->d_tc_slots, p->d_tc_units, p->d_doff, Rg.nz + 1, Rg.nr, kXChunk,
+    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk, part};
+    TcArgs atc{p->d_tc_tiles, p->d_tc_rows, p->d_tc_slots, p->d_tc_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk,
                part, p->d_status};
     for (int b = 0; b < batch; ++b) {
         const R *d = delta + int64_t(b) * ng2 * ng;
@@ -476,7 +478,7 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
             StageMark m(p, BISP_STAGE_STEP2, step2_launches(P), s);
             if constexpr (sizeof(R) == 4) {
                 if (P.tensor) {
-                    CK(launch_step2_tc(atc, dstore, P.tc_class_begin, P.tc_class_slots, s));
+                    CK(launch_step2_tc(atc, dstore, P.tc_class_begin, s));
                 } else {
                     CK(launch_step2<R>(a2, dstore, P.class_begin, s));
                 }

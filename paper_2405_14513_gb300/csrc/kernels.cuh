@@ -97,14 +97,9 @@ struct TcArgs {
     int *status;             // set to 1 by a block whose tensor-core wait ran out
 };
 
-// Dynamic shared memory of a tcgen05 Step-II block of NC = 16 (cls + 1)
-// columns staging up to nslot D1 / D2 fields.
-size_t step2_tc_smem(int cls, int nslot);
-
 // One launch per column class: units [class_begin[c], class_begin[c+1]),
-// one 128-thread block per unit.
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin,
-                            const int *class_slots, cudaStream_t s);
+// one block per unit with kTcSmem bytes of shared memory.
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin, cudaStream_t s);
 
 // S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
 template <typename A>

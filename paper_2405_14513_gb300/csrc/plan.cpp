@@ -154,10 +154,11 @@ void enumerate_pair(const HostPlan &P, int n1, int n2, PairOut &out)
     }
 }
 
-// tcgen05 tiles (see TcTile): the groups of each (grid, |n3|) in order of
-// (sign of n3, n1), their rows by the centre of their r3 run, cut greedily
-// into tiles of at most 128 rows, a window of at most 64 r3 and at most
-// kTcMaxSlots staged D1 / D2 fields; then units (tile, x chunk) by class.
+// tcgen05 tiles (see TcTile): the groups of each (grid, |n3|, signs of n1,
+// n2, n3) in order of n1, their rows by the centre of their r3 run, cut
+// greedily into tiles of at most 128 rows and a window of at most 64 r3
+// whose fields fit kTcMinStages stages of shared memory; then units (tile,
+// x chunk) by class.
 // Requires the groups' partial-sum layout.  Marks the fields the tiles read.
 template <typename UsedFn>
 std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
@@ -169,18 +170,18 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
     P.tc_slots.clear();
     P.tc_units.clear();
     P.tc_mma_products = 0;
-    for (int c = 0; c < kTcClasses; ++c) P.tc_class_slots[c] = 0;
-    std::vector<std::vector<int32_t>> pool(size_t(R.ngrid) * (nz + 1));
+    auto gflags = [](const Group &G) { return (G.n1 < 0 ? 1 : 0) | (G.n2 < 0 ? 2 : 0) | (G.n3 < 0 ? 4 : 0); };
+    std::vector<std::vector<int32_t>> pool(size_t(R.ngrid) * (nz + 1) * 8);
     for (size_t g = 0; g < P.groups.size(); ++g) {
         const Group &G = P.groups[g];
-        pool[size_t(G.lev) * (nz + 1) + (G.n3 < 0 ? -G.n3 : G.n3)].push_back(int32_t(g));
+        pool[(size_t(G.lev) * (nz + 1) + (G.n3 < 0 ? -G.n3 : G.n3)) * 8 + gflags(G)].push_back(int32_t(g));
     }
     struct Cur {
         std::vector<std::pair<int32_t, int32_t>> rows;   // (group, row index in P.rows)
         std::vector<int32_t> slots;
         int lo = 1 << 30, hi = -1;
     } cur;
-    int cur_lev = 0, cur_n3 = 0;
+    int cur_lev = 0, cur_n3 = 0, cur_flags = 0;
     auto slot_of = [&](std::vector<int32_t> &sl, int32_t key) {
         for (size_t i = 0; i < sl.size(); ++i)
             if (sl[i] == key) return int(i);
@@ -200,7 +201,10 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
         T.ncol = ((cur.hi - cur.lo + 1 + 15) / 16) * 16;
         const int64_t M2 = int64_t(T.M) * T.M;
         T.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
-        if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows) return "tcgen05 tile limits";
+        T.flags = cur_flags;
+        if (cur_flags & 1) return "tcgen05 tiles need n1 >= 0";
+        if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows || tc_stages(T.ncol, T.nslot) == 0)
+            return "tcgen05 tile limits";
         for (auto &gr : cur.rows) {
             const Group &G = P.groups[gr.first];
             const Row &rw = P.rows[gr.second];
@@ -219,26 +223,24 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
             for (int j = 0; j < rw.n; ++j) U_(cur_lev, cur_n3, rw.r3a + j) = 1;
         }
         P.tc_slots.insert(P.tc_slots.end(), cur.slots.begin(), cur.slots.end());
-        const int cls = T.ncol / 16 - 1;
-        P.tc_class_slots[cls] = std::max(P.tc_class_slots[cls], T.nslot);
         P.tc_mma_products += double(kTcRows) * T.ncol * double(M2);
         P.tc_tiles.push_back(T);
         cur = Cur{};
         return "";
     };
     for (int lv = 0; lv < R.ngrid; ++lv)
-        for (int n3 = 0; n3 <= nz; ++n3) {
-            std::vector<int32_t> &gl = pool[size_t(lv) * (nz + 1) + n3];
+        for (int n3 = 0; n3 <= nz; ++n3)
+            for (int fl = 0; fl < 8; ++fl) {
+            std::vector<int32_t> &gl = pool[(size_t(lv) * (nz + 1) + n3) * 8 + fl];
             if (gl.empty()) continue;
             std::stable_sort(gl.begin(), gl.end(), [&](int32_t a, int32_t b) {
-                const Group &A = P.groups[a], &B = P.groups[b];
-                if ((A.n3 < 0) != (B.n3 < 0)) return A.n3 >= 0;
-                return A.n1 < B.n1;
+                return P.groups[a].n1 < P.groups[b].n1;
             });
             std::string e = close();
             if (!e.empty()) return e;
             cur_lev = lv;
             cur_n3 = n3;
+            cur_flags = fl;
             for (int32_t g : gl) {
                 const Group &G = P.groups[g];
                 std::vector<int32_t> order(G.nrow);
@@ -256,8 +258,10 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
                     if (!cur.rows.empty()) {
                         const int lo = std::min(cur.lo, int(rw.r3a)), hi = std::max(cur.hi, rw.r3a + rw.n - 1);
                         const int add = (slot_of(cur.slots, k1) < 0) + (k2 != k1 && slot_of(cur.slots, k2) < 0);
-                        if (int(cur.rows.size()) >= kTcRows || hi - lo + 1 > kTcMaxCols ||
-                            int(cur.slots.size()) + add > kTcMaxSlots) {
+                        const int ncol = ((hi - lo + 1 + 15) / 16) * 16;
+                        const int ns = int(cur.slots.size()) + add;
+                        if (int(cur.rows.size()) >= kTcRows || hi - lo + 1 > kTcMaxCols || ns > kTcMaxSlots ||
+                            tc_stages(ncol, ns) == 0) {
                             e = close();
                             if (!e.empty()) return e;
                         }

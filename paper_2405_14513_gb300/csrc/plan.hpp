@@ -9,6 +9,12 @@
 
 #include "bisp.h"
 
+#if defined(__CUDACC__)
+#define BISP_HD __host__ __device__
+#else
+#define BISP_HD
+#endif
+
 namespace bisp {
 
 constexpr int kMaxRings = 64;     // N_r for N_g <= 1024 is 52
@@ -74,8 +80,30 @@ static_assert(sizeof(Tile) == 64, "Tile is copied in 16-byte pieces");
 // per tensor-memory lane), the window's stored D3 fields its B operand.
 constexpr int kTcRows = 128;
 constexpr int kTcMaxCols = 64;
-constexpr int kTcMaxSlots = 160;      // distinct D1 / D2 fields staged by a tile
+constexpr int kTcMaxSlots = 250;      // distinct D1 / D2 fields staged by a tile
 constexpr int kTcClasses = 4;         // NC = 16 (class + 1)
+constexpr int kTcTX = 16;             // grid points of one pipeline stage
+constexpr int kTcSlotBytes = kTcTX * 8 + 16;   // one staged field row (padded)
+constexpr int kTcMinStages = 3;
+constexpr int kTcMaxStages = 8;
+constexpr size_t kTcSmem = 110 * 1024;         // dynamic shared memory of a block (two per SM)
+// Shared memory of a tcgen05 block other than its stage ring: B high and
+// low parts (two buffers each), field offsets, barriers; a multiple of 128
+// bytes, so that the ring that follows is aligned for 16-byte copies.
+BISP_HD inline size_t tc_fixed_smem(int ncol, int nslot)
+{
+    return size_t(4) * ncol * kTcTX * 8 + ((8 * size_t(nslot + ncol) + 256 + 127) & ~size_t(127));
+}
+// Stages of the ring for a tile (0 if fewer than kTcMinStages fit): each
+// stage holds the tile's nslot + ncol fields and one zero row.
+BISP_HD inline int tc_stages(int ncol, int nslot)
+{
+    const size_t fixed = tc_fixed_smem(ncol, nslot);
+    if (fixed >= kTcSmem) return 0;
+    const size_t per = size_t(nslot + ncol + 1) * kTcSlotBytes;
+    const int n = int((kTcSmem - fixed) / per);
+    return n < kTcMinStages ? 0 : (n > kTcMaxStages ? kTcMaxStages : n);
+}
 struct TcRow {
     int64_t p0;                // partial sum of (x chunk 0, first combination of the run)
     int32_t stride;            // partial sums of one x chunk of the row's group (its ncombo)
@@ -91,6 +119,8 @@ struct TcTile {
     int32_t slot0, nslot;      // staged D1 / D2 fields in tc_slots: (plane << 8) | ring
     int32_t n3abs, r3lo;       // B window: rings r3lo .. r3lo + ncol - 1 of plane |n3|
     int32_t ncol, nchunk;      // NC; x chunks of the M^2 grid
+    int32_t flags;             // the rows' flags (all rows of a tile share them)
+    int32_t pad;
 };
 struct TcUnit {
     int32_t tile, chunk;
@@ -156,7 +186,6 @@ struct HostPlan {
     std::vector<int32_t> tc_slots;
     std::vector<TcUnit> tc_units;       // by class (NC), then grid, x chunk, tile
     int64_t tc_class_begin[kTcClasses + 1] = {};
-    int tc_class_slots[kTcClasses] = {};    // largest nslot of a tile of each class
     double tc_mma_products = 0;         // sum over tiles of 128 NC M^2 (lane-column-points)
     std::vector<Unit> units;            // Step-II blocks in launch order
     int max_slots = 0;                  // largest staged ring count of a unit

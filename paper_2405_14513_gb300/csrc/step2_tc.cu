@@ -11,10 +11,12 @@
 //   B[c][2x]  = Re D3,  B[c][2x + 1]  = Im D3,
 // with D3 the stored field of plane |n3| and g3 = -1 when n3 < 0 (the field
 // of a negative plane is the conjugate of the stored one; likewise g1, g2 in
-// P).  The CUDA cores form A and store it to tensor memory (lane = row); B
-// is staged in shared memory in the K-major canonical layout (core matrices
-// of 8 rows x 16 bytes, no swizzle); one thread issues the MMAs
-// (M = 128, N = NC, K = 8, kind::tf32, FP32 accumulator in tensor memory).
+// P).  The fields of a stage (16 grid points = 128 bytes each) are staged
+// in shared memory by cp.async; the CUDA cores form A and store it to
+// tensor memory (lane = row) and write B, split into high and low parts, in
+// the K-major canonical layout (core matrices of 8 rows x 16 bytes, no
+// swizzle); one thread issues the MMAs (M = 128, N = NC, K = 8, kind::tf32,
+// FP32 accumulator in tensor memory).
 //
 // Precision.  A tf32 MMA reads the top 19 bits of each FP32 operand (it
 // truncates), so every operand is split x = hi + lo with hi = x with its 13
@@ -33,9 +35,9 @@ namespace bisp {
 
 namespace {
 
-constexpr int kTX = 16;                      // grid points per stage (K = 32)
-constexpr int kSlotBytes = kTX * 8 + 16;     // one staged D1 / D2 field row, padded
-constexpr uint32_t kTmemCols = 128;          // A hi [0, 32), A lo [32, 64), D [64, 64 + NC)
+constexpr int kTX = kTcTX;                   // grid points per stage (K = 32)
+constexpr int kSlotBytes = kTcSlotBytes;
+constexpr uint32_t kTmemCols = 256;          // A[2]: hi 32 + lo 32 columns each; two accumulators of 64
 constexpr int kWaitSpins = 1 << 22;          // bound of a tensor-core completion wait
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -71,12 +73,11 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t b, uin
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16])
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
 {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n"
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
                  ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
-                   "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
-                   "r"(v[15]) : "memory");
+                   "r"(v[7]) : "memory");
 }
 
 // 16 columns of this thread's lane; the wait is in the same statement so the
@@ -91,17 +92,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "r"(taddr) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mb, uint32_t parity)
-{
-    for (int i = 0; i < kWaitSpins; ++i) {
-        uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(mb), "r"(parity) : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
 template <int NC>
 __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NC])
 {
@@ -114,8 +104,96 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NC])
     }
 }
 
+// One block per unit (tile, x chunk), warp-specialised:
+//   warps 0-3  form A (one row per thread = tensor-memory lane), write B's
+//              high and low parts, and add each stage's accumulators into
+//              FP32 registers;
+//   warps 4-5  (one thread each) issue the MMAs of a stage, six each, into
+//              two accumulators: a tcgen05.mma holds its issuing thread for
+//              tens of cycles, so two issuers per block keep the tensor
+//              cores fed;
+//   warps 6-7  stage the fields of each stage in shared memory (cp.async,
+//              a ring of 3 to 8 stages).
+// mbarriers (phase k of a barrier = its k-th use):
+//   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
+//   empty[q]  ring buffer q has been read             (128 compute arrivals)
+//   aready[b] A and B (high, low) of buffer b written (128 compute arrivals)
+//   mdone[i]  the MMAs of issuer i's stage are done   (commit)
+//   dfree     both accumulators have been read        (128 compute arrivals)
+constexpr int kThreads = 256;
+constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
+
+struct TcSync {
+    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2], dfree;
+    uint32_t tmem;
+    int abort;
+};
+static_assert(sizeof(TcSync) <= 256, "barriers fit the fixed shared-memory allowance");
+
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(m)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *m)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(su32(m)) : "memory");
+}
+
+// Bounded wait for phase `parity` of m; gives up (false) when the block is
+// aborting or after kWaitSpins polls, and then raises the abort flag.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, volatile int *abort)
+{
+    const uint32_t a = su32(m);
+    for (int i = 0; i < kWaitSpins; ++i) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+// The A columns of one stage for this thread's row: P = D1' D2' with
+// D' the stored field or its conjugate (G1, G2: n1 < 0, n2 < 0), and
+// A = (Re P, -g3 Im P) (G3: n3 < 0), high parts at column a, low parts at
+// a + 32.  u8, v8: the row's two staged fields (16 points each).
+template <bool G1, bool G2, bool G3>
+__device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned char *v8, uint32_t a)
+{
+    // Re P = ux vx - g1 g2 uy vy;  -g3 Im P = s2 ux vy + s1 uy vx,
+    // s2 = -g3 g2, s1 = -g3 g1
+    constexpr bool NEG12 = (G1 == G2);            // the uy vy term enters with -
+    constexpr bool NEG2 = !(G3 ^ G2);             // s2 = -1
+    constexpr bool NEG1 = !(G3 ^ G1);             // s1 = -1
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {                 // 4 grid points = 8 columns
+        uint32_t hi[8], lo[8];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const float4 u = *reinterpret_cast<const float4 *>(u8 + (h * 2 + k) * 16);
+            const float4 v = *reinterpret_cast<const float4 *>(v8 + (h * 2 + k) * 16);
+            float e[4];
+            const float t0 = u.y * v.y, t1 = u.y * v.x, t2 = u.w * v.w, t3 = u.w * v.z;
+            e[0] = fmaf(u.x, v.x, NEG12 ? -t0 : t0);
+            e[1] = fmaf(NEG2 ? -u.x : u.x, v.y, NEG1 ? -t1 : t1);
+            e[2] = fmaf(u.z, v.z, NEG12 ? -t2 : t2);
+            e[3] = fmaf(NEG2 ? -u.z : u.z, v.w, NEG1 ? -t3 : t3);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                hi[4 * k + j] = __float_as_uint(e[j]);
+                lo[4 * k + j] = __float_as_uint(e[j] - tf32_hi(e[j]));
+            }
+        }
+        tmem_st8(a + 8 * h, hi);
+        tmem_st8(a + 32 + 8 * h, lo);
+    }
+}
+
 template <int NC>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(kThreads, 2)
 k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
 {
     constexpr int NB = NC / 8;                   // 8-row groups of B
@@ -127,18 +205,20 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
 
     const TcUnit U = args.units[unit0 + blockIdx.x];
     const TcTile T = args.tiles[U.tile];
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int nslot = T.nslot, nf = nslot + NC;
-    // shared memory: B stages [2][BB], B lo [BB], D1 / D2 stages
-    // [2][nslot][kSlotBytes], field offsets [nf], mbarrier, tensor-memory address
-    unsigned char *sB = smem;
+    const int S = tc_stages(NC, nslot);          // ring depth (>= 3; the plan checked)
+    const int rowb = (nf + 1) * kSlotBytes;      // one ring buffer: nf fields and a zero row
+    // shared memory: B high and low parts [2][BB] each (canonical layout),
+    // field offsets [nf], barriers, ring [S][nf + 1][kSlotBytes] (D1 / D2
+    // slots, the B window, a zero row)
+    unsigned char *sHi = smem;
     unsigned char *sLo = smem + 2 * BB;
-    unsigned char *sS = smem + 3 * BB;
-    int64_t *offs = reinterpret_cast<int64_t *>(sS + 2 * size_t(nslot) * kSlotBytes);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(offs + nf);
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(mbar + 1);
+    int64_t *offs = reinterpret_cast<int64_t *>(smem + 4 * BB);
+    TcSync *sy = reinterpret_cast<TcSync *>(smem + 4 * BB + 8 * size_t(nf));
+    unsigned char *sS = smem + tc_fixed_smem(NC, nslot);
 
-    for (int f = t; f < nf; f += 128) {
+    for (int f = t; f < nf; f += kThreads) {
         int64_t o = -1;
         if (f < nslot) {
             const int32_t v = args.slots[T.slot0 + f];
@@ -150,147 +230,169 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         offs[f] = o;
     }
     if (t == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(su32(mbar)) : "memory");
+        for (int q = 0; q < S; ++q) {
+            mbar_init(&sy->full[q], 64);
+            mbar_init(&sy->empty[q], 128);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sy->aready[b], 128);
+            mbar_init(&sy->mdone[b], 1);
+        }
+        mbar_init(&sy->dfree, 128);
+        sy->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     ::"r"(su32(tslot)), "n"(kTmemCols) : "memory");
+                     ::"r"(su32(&sy->tmem)), "n"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    const bool live = t < T.nrow;
-    TcRow R{};
-    if (live) R = args.rows[T.row0 + t];
-    const float g1 = (R.flags & 1) ? -1.f : 1.f, g2 = (R.flags & 2) ? -1.f : 1.f, g3 = (R.flags & 4) ? -1.f : 1.f;
-    const float k12 = -g1 * g2, kb = -g3 * g2, ka = -g3 * g1;
+    __syncthreads();
+    // fields that are not stored (past the last ring), and the zero row, read as zero
+    for (int i = t; i < S * (nf + 1) * 8; i += kThreads) {
+        const int q = i / ((nf + 1) * 8), rem = i - q * (nf + 1) * 8, f = rem >> 3, p = rem & 7;
+        if (f < nf && offs[f] >= 0) continue;
+        *reinterpret_cast<float4 *>(sS + q * rowb + f * kSlotBytes + p * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    const uint32_t tmem = *tslot;
-    const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
-
-    // fields that are not stored (past the last ring) read as zero in both stages
-    for (int i = t; i < 2 * nf * 8; i += 128) {
-        const int b = i / (nf * 8), rem = i - b * nf * 8, f = rem >> 3, p = rem & 7;
-        if (offs[f] >= 0) continue;
-        unsigned char *d = f < nslot ? sS + (size_t(b) * nslot + f) * kSlotBytes + p * 16
-                                     : sB + b * BB + (p * NB + (f - nslot) / 8) * 128 + ((f - nslot) & 7) * 16;
-        *reinterpret_cast<float4 *>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    const uint32_t tmem = sy->tmem;
+    volatile int *abort = &sy->abort;
 
     const int64_t M2 = int64_t(T.M) * T.M;
     const int64_t x0 = int64_t(U.chunk) * args.x_chunk;
     const int64_t x1 = min(M2, x0 + args.x_chunk);
     const int nstage = int((x1 - x0) / kTX);
-    // 16-byte piece p (grid points 2p, 2p + 1) of every field for stage st;
-    // B pieces land in the canonical layout: core matrix (K block p, rows
-    // 8 (c / 8) ..), row c % 8
-    auto issue = [&](int st) {
-        const int b = st & 1;
-        const int64_t xs = x0 + int64_t(st) * kTX;
-        for (int i = t; i < nf * 8; i += 128) {
-            const int f = i >> 3, p = i & 7;
-            const int64_t o = offs[f];
-            if (o < 0) continue;
-            const uint32_t d = f < nslot ? su32(sS + (size_t(b) * nslot + f) * kSlotBytes + p * 16)
-                                         : su32(sB + b * BB + (p * NB + (f - nslot) / 8) * 128 + ((f - nslot) & 7) * 16);
-            cp_async16(d, dstore + o + xs + 2 * p);
-        }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
+    bool ok = true;
 
-    float acc[NC];
+    if (warp >= 6) {
+        // producers: lane l of the 64 copies piece p = l % 8 (grid points
+        // 2p, 2p + 1) of fields l / 8, l / 8 + 8, ...; their offsets (in
+        // 16-element units: every stored field starts at a multiple of 16)
+        // are held in registers
+        const int pl = t - 192, p = pl & 7, f0 = pl >> 3;
+        uint32_t o16[kProdFields];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = 0.f;
-    const uint32_t mb = su32(mbar);
-    int failed = 0;
-    if (nstage > 0) issue(0);
-    for (int st = 0; st < nstage; ++st) {
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        // the previous stage's MMAs read B stage (st - 1) & 1, B lo and A, and wrote D
-        int late = 0;
-        if (st > 0 && t == 0) late = !mbar_wait(mb, uint32_t(st - 1) & 1);
-        if (__syncthreads_or(late)) {
-            failed = 1;
-            break;
+        for (int k = 0; k < kProdFields; ++k) {
+            const int f = f0 + 8 * k;
+            const int64_t o = f < nf ? offs[f] : -1;
+            o16[k] = o < 0 ? 0xFFFFFFFFu : uint32_t(o >> 4);
         }
-        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (st + 1 < nstage) issue(st + 1);
-        if (st > 0) add_accumulator<NC>(tlane + 64, acc);
-        const int b = st & 1;
-        // low parts of B
-        for (int i = t; i < NC * 8; i += 128) {
-            const float4 v = *reinterpret_cast<const float4 *>(sB + b * BB + i * 16);
-            *reinterpret_cast<float4 *>(sLo + i * 16) =
-                make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+        for (int st = 0; st < nstage && ok; ++st) {
+            const int q = st % S;
+            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], uint32_t(st / S - 1) & 1, abort);
+            if (!ok) break;
+            const float2 *src = dstore + x0 + int64_t(st) * kTX + 2 * p;
+            const uint32_t dst = su32(sS + q * rowb + f0 * kSlotBytes + p * 16);
+#pragma unroll
+            for (int k = 0; k < kProdFields; ++k)
+                if (o16[k] != 0xFFFFFFFFu) cp_async16(dst + 8 * k * kSlotBytes, src + (int64_t(o16[k]) << 4));
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(&sy->full[q])) : "memory");
         }
-        // A: the row's pair products, high and low parts, to tensor memory
-        {
-            const unsigned char *p1 = sS + (size_t(b) * nslot + R.s1) * kSlotBytes;
-            const unsigned char *p2 = sS + (size_t(b) * nslot + R.s2) * kSlotBytes;
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else if (warp >= 4) {
+        // MMA issue.  Issuer 0: high A x high B over k-steps 0-3, low A x
+        // high B over k-steps 0-1; issuer 1: low A x high B over 2-3, high A
+        // x low B over 0-3; each into its own accumulator.
+        const int me = warp - 4;
+        if (lane == 0) {
+            const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
+            const uint32_t d = tmem + 128 + 64 * me;
+            for (int st = 0; st < nstage && ok; ++st) {
+                const int b = st & 1;
+                ok = mbar_wait_abort(&sy->aready[b], uint32_t(st >> 1) & 1, abort);
+                if (ok && st >= 1) ok = mbar_wait_abort(&sy->dfree, uint32_t(st - 1) & 1, abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a = tmem + 64 * b;
+                const uint64_t bo = uint64_t(b * BB) >> 4;      // start-address field offset of buffer b
+                constexpr uint64_t kstep = (2 * LBO) >> 4;      // next k-step (two core matrices along K)
+                if (me == 0) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                uint32_t hi[16], lo[16];
+                    for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dh + bo + j * kstep, ID, j > 0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 u = *reinterpret_cast<const float4 *>(p1 + (h * 4 + q) * 16);
-                    const float4 v = *reinterpret_cast<const float4 *>(p2 + (h * 4 + q) * 16);
-                    float e[4];
-                    e[0] = fmaf(u.x, v.x, k12 * (u.y * v.y));
-                    e[1] = fmaf(kb * u.x, v.y, ka * (u.y * v.x));
-                    e[2] = fmaf(u.z, v.z, k12 * (u.w * v.w));
-                    e[3] = fmaf(kb * u.z, v.w, ka * (u.w * v.z));
+                    for (int j = 0; j < 2; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
+                } else {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const float x = live ? e[j] : 0.f;
-                        hi[4 * q + j] = __float_as_uint(x);
-                        lo[4 * q + j] = __float_as_uint(x - tf32_hi(x));
-                    }
+                    for (int j = 2; j < 4; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, j > 2);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dl + bo + j * kstep, ID, 1);
                 }
-                tmem_st16(tlane + 16 * h, hi);
-                tmem_st16(tlane + 32 + 16 * h, lo);
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                             ::"r"(su32(&sy->mdone[me])) : "memory");
             }
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        __syncthreads();
-        if (t == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t bh = su32(sB + b * BB), bl = su32(sLo), d = tmem + 64;
+        __syncwarp();
+    } else {
+        // compute warps: thread t owns tensor-memory lane t (row t of the tile);
+        // rows past the tile's end read the zero row
+        const bool live = t < T.nrow;
+        TcRow R{};
+        if (live) R = args.rows[T.row0 + t];
+        const int s1 = live ? R.s1 : nf, s2 = live ? R.s2 : nf;
+        const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
+        float acc[NC];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mma_tf32(d, tmem + 8 * j, smem_desc(bh + 2 * j * LBO, LBO, SBO), ID, j > 0);
+        for (int c = 0; c < NC; ++c) acc[c] = 0.f;
+        for (int st = 0; st <= nstage && ok; ++st) {
+            if (st < nstage) {
+                const int q = st % S, b = st & 1;
+                ok = mbar_wait_abort(&sy->full[q], uint32_t(st / S) & 1, abort);
+                if (!ok) break;
+                const unsigned char *sq = sS + q * rowb;
+                // B, high and low parts, in the canonical layout: piece p (grid
+                // points 2p, 2p + 1) of column c goes to core matrix (K block p,
+                // rows 8 (c / 8) ..), row c % 8.  Buffer b was last read by the
+                // MMAs of stage st - 2, complete: their accumulators were read
+                // at stage st - 1.
+                for (int i = t; i < NC * 8; i += 128) {
+                    const int c = i % NC, p = i / NC;
+                    const float4 v = *reinterpret_cast<const float4 *>(sq + (nslot + c) * kSlotBytes + p * 16);
+                    const int o = b * BB + (p * NB + c / 8) * 128 + (c % 8) * 16;
+                    *reinterpret_cast<float4 *>(sHi + o) = v;
+                    *reinterpret_cast<float4 *>(sLo + o) =
+                        make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+                }
+                const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
+                const uint32_t a = tlane + 64 * b;
+                switch (T.flags) {   // uniform over the tile; n1 >= 0 (half space)
+                case 0: form_a<false, false, false>(u8, v8, a); break;
+                case 2: form_a<false, true, false>(u8, v8, a); break;
+                case 4: form_a<false, false, true>(u8, v8, a); break;
+                default: form_a<false, true, true>(u8, v8, a); break;
+                }
+                mbar_arrive(&sy->empty[q]);
+                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                mbar_arrive(&sy->aready[b]);
+            }
+            if (st > 0) {
+                // accumulators of stage st - 1
+                const uint32_t par = uint32_t(st - 1) & 1;
+                ok = mbar_wait_abort(&sy->mdone[0], par, abort) && mbar_wait_abort(&sy->mdone[1], par, abort);
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                add_accumulator<NC>(tlane + 128, acc);
+                add_accumulator<NC>(tlane + 192, acc);
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                mbar_arrive(&sy->dfree);
+            }
+        }
+        if (live) {
+            double *dst = args.partials + R.p0 + int64_t(U.chunk) * R.stride;
+            const double nan = __longlong_as_double(0x7FF8000000000000LL);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) mma_tf32(d, tmem + 32 + 8 * j, smem_desc(bh + 2 * j * LBO, LBO, SBO), ID, 1);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) mma_tf32(d, tmem + 8 * j, smem_desc(bl + 2 * j * LBO, LBO, SBO), ID, 1);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                         ::"r"(mb) : "memory");
+            for (int c = 0; c < NC; ++c) {
+                const int j = c - int(R.col0);
+                if (j >= 0 && j < int(R.n)) dst[j] = ok ? double(acc[c]) : nan;
+            }
         }
     }
-    if (!failed && nstage > 0) {
-        int late = 0;
-        if (t == 0) late = !mbar_wait(mb, uint32_t(nstage - 1) & 1);
-        if (__syncthreads_or(late)) {
-            failed = 1;
-        } else {
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            add_accumulator<NC>(tlane + 64, acc);
-        }
-    }
-    if (live) {
-        double *dst = args.partials + R.p0 + int64_t(U.chunk) * R.stride;
-        const double nan = __longlong_as_double(0x7FF8000000000000LL);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const int j = c - int(R.col0);
-            if (j >= 0 && j < int(R.n)) dst[j] = failed ? nan : double(acc[c]);
-        }
-    }
-    if (failed && t == 0) atomicExch(args.status, 1);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    if (t == 0 && *abort) atomicExch(args.status, 1);
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(kTmemCols) : "memory");
@@ -298,32 +400,23 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
 }
 
 template <int NC>
-cudaError_t launch_class(const TcArgs &a, const float2 *dstore, int64_t u0, int64_t n, size_t smem, cudaStream_t s)
+cudaError_t launch_class(const TcArgs &a, const float2 *dstore, int64_t u0, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_step2_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaError_t e = cudaFuncSetAttribute(k_step2_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
     if (e != cudaSuccess) return e;
-    k_step2_tc<NC><<<unsigned(n), 128, smem, s>>>(a, u0, dstore);
+    k_step2_tc<NC><<<unsigned(n), kThreads, kTcSmem, s>>>(a, u0, dstore);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t step2_tc_smem(int cls, int nslot)
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *cb, cudaStream_t s)
 {
-    const int nc = 16 * (cls + 1);
-    const size_t need = size_t(3) * nc * kTX * 8 + size_t(2) * nslot * kSlotBytes + 8 * size_t(nslot + nc) + 16;
-    // at least 56 KB so that at most four blocks (4 x 128 tensor-memory
-    // columns) share an SM
-    return std::max<size_t>(need, 56 * 1024);
-}
-
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *cb, const int *cs, cudaStream_t s)
-{
-    cudaError_t e = launch_class<16>(a, dstore, cb[0], cb[1] - cb[0], step2_tc_smem(0, cs[0]), s);
-    if (e == cudaSuccess) e = launch_class<32>(a, dstore, cb[1], cb[2] - cb[1], step2_tc_smem(1, cs[1]), s);
-    if (e == cudaSuccess) e = launch_class<48>(a, dstore, cb[2], cb[3] - cb[2], step2_tc_smem(2, cs[2]), s);
-    if (e == cudaSuccess) e = launch_class<64>(a, dstore, cb[3], cb[4] - cb[3], step2_tc_smem(3, cs[3]), s);
+    cudaError_t e = launch_class<16>(a, dstore, cb[0], cb[1] - cb[0], s);
+    if (e == cudaSuccess) e = launch_class<32>(a, dstore, cb[1], cb[2] - cb[1], s);
+    if (e == cudaSuccess) e = launch_class<48>(a, dstore, cb[2], cb[3] - cb[2], s);
+    if (e == cudaSuccess) e = launch_class<64>(a, dstore, cb[3], cb[4] - cb[3], s);
     return e;
 }
 
