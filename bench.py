@@ -4,7 +4,10 @@ multipoles B_l^m(k1, mu, t) on its headline workload.
 
 Workload: N_g = 512, L = 2000 Mpc/h, 30 linear k1 bins over
 [(N_g/12) k_f, (N_g/3) k_f], (mu, t) step 0.025 on [0.5, 1] (20 x 20 bins),
-l <= 6 (16 moments), FP32 transforms and products with FP64 sums ("mixed").
+l <= 6 (16 moments).  Default precision "mixed_tc": FP32 transforms, the
+Step-II triple sums on the tcgen05 tensor cores with each FP32 operand split
+into TF32 high and low parts (FP32 accuracy), FP64 across chunks and in the
+binning; --precision mixed runs Step II on the FP32 CUDA cores instead.
 The input is the seeded synthetic non-Gaussian redshift-space field (P(k) =
 A k^-2, sigma_G = 0.1, f_NG = 0.5, Kaiser beta = 0.5).
 
@@ -14,7 +17,7 @@ bin carrying all 16 moments ("configs/s").  Each rank estimates its own
 field (independent problems, no collective in the data path): value is
 (ranks x bins) / max-over-ranks time, "scaling": "weak".
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision P]
 
 --impl reference times the FP64 CPU oracle (the only other implementation
 of the method; the paper publishes no code) on a bounded sample of the same
@@ -38,15 +41,24 @@ sys.path.insert(0, ROOT)
 
 NG, BOX, NK1, NMU, LMAX = 512, 2000.0, 30, 20, 6
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
 METRIC = "B_l^m(k1,mu,t) configs/s at N_g=512"
 
 
-def workload(ng):
+PRECISION_TEXT = {
+    "mixed_tc": "FP32 transforms; Step-II products on tcgen05 tensor cores (TF32 high/low split, 3 passes, FP32 accuracy); FP32 sums per 16384-point chunk, FP64 across chunks and in the binning",
+    "mixed": "FP32 transforms and products on CUDA cores, FP64 sums",
+    "fp32": "FP32 throughout",
+    "fp64": "FP64 throughout",
+}
+
+
+def workload(ng, precision="mixed_tc"):
     from paper_2405_14513_gb300 import synth
     return {"workload": f"redshift-space bispectrum multipoles, N_g={ng}^3, L={BOX:g} Mpc/h, "
                         f"{NK1} linear k1 bins, (mu,t) step 0.025 ({NMU}x{NMU}), l<=6 (16 moments)",
             "n_g": ng, "box_len": BOX, "n_k1": NK1, "n_mu": NMU, "n_t": NMU, "l_max": LMAX,
-            "precision": "mixed (FP32 transforms/products, FP64 sums)",
+            "precision": f"{precision}: {PRECISION_TEXT[precision]}",
             "field": "seeded synthetic: P=A k^-2, sigma_G=0.1, f_NG=0.5, Kaiser beta=0.5",
             "l2": "inputs and D-field store larger than L2 (no flush needed)"}, \
         synth.default_k1_edges(ng, BOX, NK1)
@@ -128,23 +140,39 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def _traffic(ng):
-    """DRAM bytes per Step-II launch from the committed ncu summary, if any."""
-    p = os.path.join(ROOT, "profiles", "step2_dram.json")
+# source file of the Step-II kernel of each precision mode
+STEP2_SOURCE = {"mixed_tc": "step2_tc.cu", "mixed": "kernels.cu", "fp32": "kernels.cu", "fp64": "kernels.cu"}
+
+
+def _traffic(ng, precision):
+    """DRAM bytes of Step II per estimate from the committed ncu summary, if
+    it was taken on the kernel source as it is now."""
+    p = os.path.join(ROOT, "profiles", f"step2_dram_{precision}.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
-        if d.get("kernel_digest") != _kernel_digest():
+        if d.get("kernel_digest") != _kernel_digest(precision) or int(d.get("n_g", ng)) != ng:
             return None
-        return float(d["bytes_per_launch"]) * float(d.get("scale_to_ng", {}).get(str(ng), 1.0))
+        return float(d["bytes_per_estimate"])
     except (OSError, ValueError, KeyError):
         return None
 
 
-def _kernel_digest():
+def _kernel_digest(precision):
     import hashlib
-    with open(os.path.join(ROOT, "paper_2405_14513_gb300", "csrc", "kernels.cu"), "rb") as fh:
+    src = os.path.join(ROOT, "paper_2405_14513_gb300", "csrc", STEP2_SOURCE[precision])
+    with open(src, "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def _peaks():
+    """Measured peaks of this GPU type (written by the harness), or the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, 6800.0, "fallback"
 
 
 # ----------------------------------------------------------------------------
@@ -203,7 +231,7 @@ def run_reference(args):
         return 0
     from paper_2405_14513_gb300 import synth
     ng = args.ng
-    cfg, edges = workload(ng)
+    cfg, edges = workload(ng, args.precision)
     n_bins = NK1 * NMU * NMU
     field64 = synth.make_field(ng, BOX, 1).astype(np.float32).astype(np.float64)
     vals, walls = [], []
@@ -239,8 +267,8 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
     ng = args.ng
-    cfg, edges = workload(ng)
-    plan = api.Plan(ng, BOX, edges, NMU, NMU, LMAX, precision="mixed", max_batch=1)
+    cfg, edges = workload(ng, args.precision)
+    plan = api.Plan(ng, BOX, edges, NMU, NMU, LMAX, precision=args.precision, max_batch=1)
     field = synth.make_field_torch(ng, BOX, 1 + rank, device=dev).to(torch.float32).contiguous()
     ws = plan.workspace(1, device=dev)
     out = torch.empty(plan.out_shape(1), dtype=torch.float64, device=dev)
@@ -292,15 +320,24 @@ def run_ours(args):
 
     # roofline of the dominant kernel (Step II), from its own events
     # Step II runs as one launch per block class; its time per estimate is the
-    # sum of those launches, timed by events on the launching stream
+    # sum of those launches, timed by events on the launching stream.  The
+    # algorithmic flops are the method's real arithmetic: 4 per grid point of
+    # each combination (Re of a complex product) + 6 per grid point of each
+    # distinct pair product.
     s2_ms = st_ms["step2"] / args.steps
     achieved = flops["step2"] / (s2_ms / 1e3) / 1e12
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-    roof = {"kernel": "k_step2 (Step II triple sums)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": _traffic(ng),
-            "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)",
-            "flops_per_estimate": flops["step2"], "ms_per_estimate": s2_ms,
-            "launches_per_estimate": st_n["step2"] / args.steps}
+    bf16, _, src = _peaks()
+    if args.precision == "mixed_tc":
+        peak = bf16 * TF32_PER_BF16
+        roof = {"kernel": "k_step2_tc (Step II triple sums, tcgen05 kind::tf32)", "bound": "tensor",
+                "peak_source": f"tf32 dense: bf16 burst of {src} x {TF32_PER_BF16:.4f} (nominal 1.1 / 2.25 PFLOP/s)"}
+    else:
+        peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        roof = {"kernel": "k_step2 (Step II triple sums, FP32 FMA)", "bound": "alu",
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"}
+    roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                 "traffic": _traffic(ng, args.precision), "flops_per_estimate": flops["step2"],
+                 "ms_per_estimate": s2_ms, "launches_per_estimate": st_n["step2"] / args.steps})
     stage_share = {k: st_ms[k] / max(sum(st_ms.values()), 1e-9) for k in st_ms}
     launches = int(sum(st_n.values()))
 
@@ -332,6 +369,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ng", type=int, default=NG, help="grid size (the headline workload is 512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
+                    help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)

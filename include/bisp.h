@@ -126,6 +126,13 @@ int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *work
 int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
                             void *stream);
 
+/* Device-side status of the plan's kernels: synchronises `stream`, then
+ * returns BISP_TIMEOUT if a tensor-core block of an earlier estimate gave up
+ * a bounded wait (its combinations then hold NaN), else BISP_OK; the status
+ * is cleared.  estimator_estimate_host checks it after every call.  (The
+ * paper has no counterpart: this reports the library's own wait bounds.) */
+int estimator_device_status(bisp_plan *plan, void *stream);
+
 /* Release the plan and everything it owns (NULL is a no-op).  The caller
  * makes sure no work that uses the plan is still running. */
 void estimator_destroy(bisp_plan *plan);

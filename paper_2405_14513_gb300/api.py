@@ -77,6 +77,8 @@ def load():
         lib.estimator_dfield.restype = C.c_int
         lib.estimator_delta_plane.argtypes = [vp, vp, C.c_int, dp, vp]
         lib.estimator_delta_plane.restype = C.c_int
+        lib.estimator_device_status.argtypes = [vp, vp]
+        lib.estimator_device_status.restype = C.c_int
         lib.estimator_set_timing.argtypes = [vp, C.c_int]
         lib.estimator_set_timing.restype = C.c_int
         lib.estimator_stage_times.argtypes = [vp, dp, vp]
@@ -209,6 +211,11 @@ class Plan:
         if got != n:
             raise BispError(6, "estimator_combo_table", "count mismatch")
         return {"ints": ints[:n], "ntri": ntri[:n], "bin": binv[:n], "grid": grid[:n]}
+
+    def device_status(self, stream=None) -> int:
+        """Synchronise the stream; BISP status of the plan's kernels since the
+        last query (5 = a bounded tensor-core wait gave up), then cleared."""
+        return int(load().estimator_device_status(self._h, _stream_handle(stream)))
 
     def combo_sums(self, workspace, stream=None) -> np.ndarray:
         S = np.zeros(max(self.n_combos, 1))

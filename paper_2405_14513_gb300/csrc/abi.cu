@@ -600,8 +600,20 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
     int st = dispatch_estimate(p, p->own_in, batch, p->own_ws, p->own_out, s);
     if (st) return st;
     CK(cudaMemcpyAsync(B_host, p->own_out, outb * batch, cudaMemcpyDeviceToHost, s));
+    return estimator_device_status(p, stream);
+}
+
+int estimator_device_status(bisp_plan *p, void *stream)
+{
+    if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return BISP_OK;
+    if (h == 0) return BISP_OK;
+    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return fail(BISP_TIMEOUT, "a tensor-core Step-II block gave up a bounded wait; its sums are NaN");
 }
 
 void estimator_destroy(bisp_plan *p) { free_plan(p); }

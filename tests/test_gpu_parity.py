@@ -191,3 +191,71 @@ def test_ragged_and_degenerate_configurations():
             assert floored_rel_err(c.B, ref).max() < TOL["fp64"]
         else:
             assert not np.isfinite(c.B).any()
+
+
+# --------------------------------------------------------------------------
+# Step II on tcgen05 (precision "mixed_tc", the benchmark's path)
+# --------------------------------------------------------------------------
+def test_tensor_core_ragged_and_degenerate_configurations():
+    """The tcgen05 path on the smallest grid, one k1 bin, l_max = 0, one
+    (mu, t) bin, empty bins, and a grid whose tiles hold few rows."""
+    for ng, L, edges, nmu, nt, lmax in [
+        (8, 100.0, None, 1, 1, 0),
+        (32, 500.0, np.array([0.03, 0.1, 0.12]), 3, 7, 2),
+        (32, 500.0, synth.default_k1_edges(32, 500.0, 1), 16, 16, 8),
+        (16, 300.0, None, 4, 4, 4),
+    ]:
+        if edges is None:
+            edges = synth.default_k1_edges(ng, L, 1)
+        c = Case(ng, L, len(edges) - 1, nmu, nt, lmax, precision="mixed_tc", edges=edges, seed=7)
+        assert c.plan.device_status() == 0
+        ref = O.select_even(c.oracle["B"], lmax)
+        if np.isfinite(ref).any():
+            assert floored_rel_err(c.B, ref).max() < TOL["mixed_tc"]
+        else:
+            assert not np.isfinite(c.B).any()
+
+
+def test_tensor_core_128_sampled_sums_and_cuda_core_agreement():
+    """128^3 with 20 x 20 (mu, t) bins, several tiles per window class and
+    every reduction grid: sampled Re S against the oracle, and B against the
+    CUDA-core FP32 path."""
+    ng, L = 128, 500.0
+    tc = Case(ng, L, 12, 20, 20, 6, precision="mixed_tc", seed=11)
+    assert tc.plan.device_status() == 0
+    tab = tc.plan.combo_table()
+    S = tc.plan.combo_sums(tc.ws)
+    pick = np.random.default_rng(12).choice(len(S), size=300, replace=False)
+    want = O.combo_sums(tc.field64, L, tab["ints"][pick]).real
+    assert np.abs(S[pick] - want).max() < TOL["mixed_tc"] * np.sqrt(np.mean(want ** 2))
+    cc = Case(ng, L, 12, 20, 20, 6, precision="mixed", seed=11)
+    assert floored_rel_err(tc.B, cc.B).max() < 2 * TOL["mixed_tc"]
+
+
+@pytest.mark.slow
+def test_tensor_core_full_size_512_sampled():
+    """The benchmark's workload and launch configuration (512^3, L = 2000,
+    30 k1 bins, 20 x 20 (mu, t), l <= 6, mixed_tc): Re S of sampled
+    combinations, spread over the reduction grids, against the oracle."""
+    ng, L = 512, 2000.0
+    edges = synth.default_k1_edges(ng, L, 30)
+    plan = api.Plan(ng, L, edges, 20, 20, 6, precision="mixed_tc")
+    ws = plan.workspace(1)
+    fd = synth.make_field_torch(ng, L, 1, device="cuda").float().contiguous()
+    field = fd.cpu().numpy()                      # the values the GPU sees, for the oracle
+    B = plan.estimate(fd[None], ws).cpu().numpy()[0]
+    assert plan.device_status() == 0
+    assert np.isfinite(B).any() and not np.isnan(B[np.isfinite(B)]).any()
+    tab = plan.combo_table()
+    S = plan.combo_sums(ws)
+    rng = np.random.default_rng(13)
+    pick = []
+    for M in np.unique(tab["grid"]):
+        idx = np.flatnonzero(tab["grid"] == M)
+        pick.extend(rng.choice(idx, size=min(3, len(idx)), replace=False))
+    pick = np.array(pick)
+    want = O.combo_sums(field.astype(np.float64), L, tab["ints"][pick]).real
+    # error relative to the magnitude a sum of M^2 terms of this size reaches
+    scale = np.sqrt(np.mean(want ** 2))
+    assert np.abs(S[pick] - want).max() < TOL["mixed_tc"] * scale
+    plan.close()
