@@ -39,10 +39,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NG, BOX, NK1, NMU, LMAX = 512, 2000.0, 30, 20, 6
+LMAX = 6
+# the workloads of the paper's method at three sizes (c3 is the headline);
+# (mu, t) bins of step 0.025 (20 x 20) or 0.1 (5 x 5) on [0.5, 1]
+WORKLOADS = {
+    "c3": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 20},
+    "c2": {"ng": 256, "box": 1000.0, "nk1": 20, "nmu": 20},
+    "c1": {"ng": 64, "box": 1000.0, "nk1": 6, "nmu": 5},
+}
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
-METRIC = "B_l^m(k1,mu,t) configs/s at N_g=512"
+METRIC = "B_l^m(k1,mu,t) configs/s at N_g={ng}"
 
 
 PRECISION_TEXT = {
@@ -53,15 +60,16 @@ PRECISION_TEXT = {
 }
 
 
-def workload(ng, precision="mixed_tc"):
+def workload(W, precision="mixed_tc"):
     from paper_2405_14513_gb300 import synth
-    return {"workload": f"redshift-space bispectrum multipoles, N_g={ng}^3, L={BOX:g} Mpc/h, "
-                        f"{NK1} linear k1 bins, (mu,t) step 0.025 ({NMU}x{NMU}), l<=6 (16 moments)",
-            "n_g": ng, "box_len": BOX, "n_k1": NK1, "n_mu": NMU, "n_t": NMU, "l_max": LMAX,
+    ng, box, nk1, nmu = W["ng"], W["box"], W["nk1"], W["nmu"]
+    return {"workload": f"redshift-space bispectrum multipoles, N_g={ng}^3, L={box:g} Mpc/h, "
+                        f"{nk1} linear k1 bins, (mu,t) step {0.5 / nmu:g} ({nmu}x{nmu}), l<=6 (16 moments)",
+            "n_g": ng, "box_len": box, "n_k1": nk1, "n_mu": nmu, "n_t": nmu, "l_max": LMAX,
             "precision": f"{precision}: {PRECISION_TEXT[precision]}",
             "field": "seeded synthetic: P=A k^-2, sigma_G=0.1, f_NG=0.5, Kaiser beta=0.5",
             "l2": "inputs and D-field store larger than L2 (no flush needed)"}, \
-        synth.default_k1_edges(ng, BOX, NK1)
+        synth.default_k1_edges(ng, box, nk1)
 
 
 # ----------------------------------------------------------------------------
@@ -176,15 +184,15 @@ def _peaks():
 
 
 # ----------------------------------------------------------------------------
-def oracle_table(ng, edges):
+def oracle_table(W, edges):
     """The oracle's combination table (its own triangle counts, Eq. Ntri2) and its wall time."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    c = O.combos(ng, BOX, edges, NMU, NMU, half_space=True, nthreads=os.cpu_count() or 1)
+    c = O.combos(W["ng"], W["box"], edges, W["nmu"], W["nmu"], half_space=True, nthreads=os.cpu_count() or 1)
     return c, time.perf_counter() - t0
 
 
-def cpu_baseline(ng, edges, field64, n_bins, sample_pairs=2, seed=0, table=None):
+def cpu_baseline(W, edges, field64, n_bins, sample_pairs=2, seed=0, table=None):
     """The FP64 oracle, as it stands, on a bounded sample of the workload.
 
     The oracle enumerates the combinations (its own triangle counts, Eq.
@@ -195,8 +203,9 @@ def cpu_baseline(ng, edges, field64, n_bins, sample_pairs=2, seed=0, table=None)
     combinations of both signs of n (the oracle enumerates both)."""
     from oracle import oracle as O
     nthreads = os.cpu_count() or 1
+    ng = W["ng"]
     t0 = time.perf_counter()
-    c, t_tab = table if table is not None else oracle_table(ng, edges)
+    c, t_tab = table if table is not None else oracle_table(W, edges)
     ints = c["ints"]
     n_half = len(ints)
     n_self = int(np.sum((ints[:, 0] == 0) & (ints[:, 1] == 0)))
@@ -210,7 +219,7 @@ def cpu_baseline(ng, edges, field64, n_bins, sample_pairs=2, seed=0, table=None)
     sample = np.concatenate([ints[a:b] for a, b in zip(starts, np.r_[starts[1:], n_half])
                              if int(key[a]) in pk])
     times = []
-    O.combo_sums(field64, BOX, sample, nthreads=nthreads, times=times)
+    O.combo_sums(field64, W["box"], sample, nthreads=nthreads, times=times)
     t_planes, t_fields, t_sums = times
     nr = len(O.rings(ng)[1])
     nz = ng // 3
@@ -230,19 +239,19 @@ def run_reference(args):
     if rank != 0:
         return 0
     from paper_2405_14513_gb300 import synth
-    ng = args.ng
-    cfg, edges = workload(ng, args.precision)
-    n_bins = NK1 * NMU * NMU
-    field64 = synth.make_field(ng, BOX, 1).astype(np.float32).astype(np.float64)
+    W = WORKLOADS[args.workload]
+    cfg, edges = workload(W, args.precision)
+    n_bins = W["nk1"] * W["nmu"] * W["nmu"]
+    field64 = synth.make_field(W["ng"], W["box"], 1).astype(np.float32).astype(np.float64)
     vals, walls = [], []
-    table = oracle_table(ng, edges)
+    table = oracle_table(W, edges)
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(ng, edges, field64, n_bins, sample_pairs=1, seed=i, table=table)
+        r = cpu_baseline(W, edges, field64, n_bins, sample_pairs=1, seed=i, table=table)
         if i >= args.warmup:
             vals.append(r["value"])
             walls.append(r["wall_s"])
     value = statistics.median(vals)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "configs/s",
+    line = {"impl": "reference", "metric": METRIC.format(ng=W["ng"]), "value": value, "unit": "configs/s",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": n_bins / value * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
@@ -266,10 +275,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    ng = args.ng
-    cfg, edges = workload(ng, args.precision)
-    plan = api.Plan(ng, BOX, edges, NMU, NMU, LMAX, precision=args.precision, max_batch=1)
-    field = synth.make_field_torch(ng, BOX, 1 + rank, device=dev).to(torch.float32).contiguous()
+    W = WORKLOADS[args.workload]
+    ng = W["ng"]
+    cfg, edges = workload(W, args.precision)
+    plan = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=1)
+    field = synth.make_field_torch(ng, W["box"], 1 + rank, device=dev).to(torch.float32).contiguous()
     ws = plan.workspace(1, device=dev)
     out = torch.empty(plan.out_shape(1), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -341,7 +351,7 @@ def run_ours(args):
     stage_share = {k: st_ms[k] / max(sum(st_ms.values()), 1e-9) for k in st_ms}
     launches = int(sum(st_n.values()))
 
-    line = {"metric": METRIC, "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC.format(ng=ng), "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "e2e": e2e, "roofline": roof, "gpu_launches": launches, "clocks": clk,
@@ -353,7 +363,7 @@ def run_ours(args):
         f64 = field.double().cpu().numpy()
         del ws
         torch.cuda.empty_cache()
-        line["cpu_baseline"] = cpu_baseline(ng, edges, f64, plan.n_bins)
+        line["cpu_baseline"] = cpu_baseline(W, edges, f64, plan.n_bins)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -367,7 +377,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--ng", type=int, default=NG, help="grid size (the headline workload is 512)")
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
+                    help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, 6 bins")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
                     help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
