@@ -46,6 +46,9 @@ WORKLOADS = {
     "c3": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 20},
     "c2": {"ng": 256, "box": 1000.0, "nk1": 20, "nmu": 20},
     "c1": {"ng": 64, "box": 1000.0, "nk1": 6, "nmu": 5},
+    # batched mocks: 256 seeded realisations, one plan, batches of 16 fields
+    # per launch, each batch a captured CUDA graph
+    "c4": {"ng": 128, "box": 500.0, "nk1": 12, "nmu": 10, "mocks": 256, "batch": 16},
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
@@ -371,6 +374,94 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Batched mocks (c4): every mock of the workload through one plan, in
+    batches of W["batch"] fields per launch, each batch a captured CUDA graph;
+    beside it, the same mocks one by one through estimator_estimate (the
+    plain single-job form).  One step = all mocks."""
+    import torch
+
+    from paper_2405_14513_gb300 import api, synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    W = WORKLOADS[args.workload]
+    ng, nm, G = W["ng"], W["mocks"], W["batch"]
+    cfg, edges = workload(W, args.precision)
+    cfg.update({"mocks": nm, "batch_per_launch": G, "graphs": nm // G,
+                "l2": "fields (2.1 GB) and D stores larger than L2 (no flush needed)"})
+    fields = torch.empty((nm, ng, ng, ng), dtype=torch.float32, device=dev)
+    for i in range(nm):
+        fields[i] = synth.make_field_torch(ng, W["box"], 1000 * rank + i + 1, device=dev).float()
+    plan = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=G)
+    ws = plan.workspace(G, device=dev)
+    out = torch.empty(plan.out_shape(nm), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)
+    graphs = [plan.graph(fields[j:j + G], ws, out[j:j + G], stream=stream) for j in range(0, nm, G)]
+
+    def step():
+        for g in graphs:
+            g.launch(stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    clocks = ClockSampler(index=local) if rank == 0 else None
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    stream.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
+    value = job_rate(nm * plan.n_bins, world, ms / 1e3)
+    status = plan.device_status(stream)
+
+    # the plain single-job form: the same mocks one by one, no graph
+    plan1 = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=1)
+    ws1 = plan1.workspace(1, device=dev)
+    out1 = torch.empty(plan1.out_shape(nm), dtype=torch.float64, device=dev)
+    for i in range(min(nm, 8)):
+        plan1.estimate(fields[i:i + 1], ws1, out=out1[i:i + 1], stream=stream)
+    stream.synchronize()
+    t0.record(stream)
+    for i in range(nm):
+        plan1.estimate(fields[i:i + 1], ws1, out=out1[i:i + 1], stream=stream)
+    t1.record(stream)
+    stream.synchronize()
+    ms1 = max_over_ranks(t0.elapsed_time(t1), device=dev)
+    same = bool(torch.equal(torch.nan_to_num(out, nan=-1.0), torch.nan_to_num(out1, nan=-1.0)))
+
+    # end to end: pinned host fields in, results out, copies timed
+    host = fields.cpu().pin_memory()
+    out_h = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        fields.copy_(host, non_blocking=True)
+        step()
+        out_h.copy_(out, non_blocking=True)
+        stream.synchronize()
+    te = max_over_ranks((time.perf_counter() - te) / args.steps, device=dev)
+    line = {"metric": f"B_l^m(k1,mu,t) configs/s, {nm} mocks at N_g={ng} (batched, CUDA graphs)",
+            "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic", "config": cfg,
+            "e2e": {"value": job_rate(nm * plan.n_bins, world, te), "unit": "configs/s",
+                    "h2d_bytes_per_step": int(host.numel() * 4), "d2h_bytes_per_step": int(out_h.numel() * 8)},
+            "single_job": {"value": job_rate(nm * plan.n_bins, world, ms1 / 1e3), "unit": "configs/s",
+                           "ms_per_step": ms1, "form": "estimator_estimate, one mock per call, no graph"},
+            "batched_over_single": ms1 / ms, "results_identical_to_single_job": same,
+            "device_status": status, "clocks": clk,
+            "gpu_launches": len(graphs) * (3 + 2 * plan.info["n_levels"] + 3 + 2)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for g in graphs:
+        g.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -378,13 +469,16 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
-                    help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, 6 bins")
+                    help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, "
+                         "6 bins; c4: 256 mocks of 128^3 in batched graphs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
                     help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if "mocks" in WORKLOADS[args.workload]:
+        return run_batched(args)
     return run_ours(args)
 
 

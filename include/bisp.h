@@ -76,7 +76,7 @@ typedef struct {
     int n_mu, n_t;            /* uniform mu and t bins on [0.5, 1], each >= 1      */
     int l_max;                /* even, 0..8                                        */
     int precision;            /* bisp_precision                                    */
-    int max_batch;            /* largest batch passed to estimator_estimate, >= 1  */
+    int max_batch;            /* largest batch passed to estimator_estimate, 1..65535 */
 } bisp_desc;
 
 typedef struct {
@@ -104,8 +104,9 @@ int estimator_plan(bisp_plan **out, const bisp_desc *desc, void *stream);
 int estimator_plan_info(const bisp_plan *plan, bisp_plan_info *info);
 
 /* Bytes of device workspace estimator_estimate needs for `batch` fields
- * (0 on a bad argument).  Fields of a batch run one after the other and
- * share the workspace, so the size does not grow with batch. */
+ * (0 on a bad argument): batch regions of one field's size.  All fields of
+ * a batch go through every stage in the same kernel launches (one more
+ * grid dimension), each in its own region. */
 size_t estimator_workspace_bytes(const bisp_plan *plan, int batch);
 
 /* Estimate B_l^m for `batch` fields (1 <= batch <= max_batch).
@@ -125,6 +126,27 @@ int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *work
  * its own device workspace and staging buffers for max_batch fields. */
 int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
                             void *stream);
+
+/* ---------------- captured estimates (CUDA graphs) ---------------- */
+
+typedef struct bisp_graph bisp_graph;
+
+/* Capture the launches of one estimator_estimate(plan, delta, batch,
+ * workspace, B) into a CUDA graph and instantiate it; the arguments keep
+ * their meaning and must stay valid while the graph exists.  Capture runs
+ * on `stream` (or, when it is NULL, on a stream of the library's); nothing
+ * is computed.  Stage timing is off while capturing.  *out is NULL on
+ * failure.  (The paper has no counterpart: this removes the per-launch
+ * host cost when many fields are estimated with one plan.) */
+int estimator_graph_create(bisp_graph **out, bisp_plan *plan, const void *delta, int batch, void *workspace,
+                           double *B, void *stream);
+
+/* Run a captured estimate on `stream` (asynchronous, stream-ordered). */
+int estimator_graph_launch(bisp_graph *graph, void *stream);
+
+/* Release a captured estimate (NULL is a no-op); no launch of it may still
+ * be running. */
+void estimator_graph_destroy(bisp_graph *graph);
 
 /* Device-side status of the plan's kernels: synchronises `stream`, then
  * returns BISP_TIMEOUT if a tensor-core block of an earlier estimate gave up

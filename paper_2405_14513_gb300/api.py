@@ -77,6 +77,12 @@ def load():
         lib.estimator_dfield.restype = C.c_int
         lib.estimator_delta_plane.argtypes = [vp, vp, C.c_int, dp, vp]
         lib.estimator_delta_plane.restype = C.c_int
+        lib.estimator_graph_create.argtypes = [C.POINTER(vp), vp, vp, C.c_int, vp, vp, vp]
+        lib.estimator_graph_create.restype = C.c_int
+        lib.estimator_graph_launch.argtypes = [vp, vp]
+        lib.estimator_graph_launch.restype = C.c_int
+        lib.estimator_graph_destroy.argtypes = [vp]
+        lib.estimator_graph_destroy.restype = None
         lib.estimator_device_status.argtypes = [vp, vp]
         lib.estimator_device_status.restype = C.c_int
         lib.estimator_set_timing.argtypes = [vp, C.c_int]
@@ -110,6 +116,27 @@ def _stream_handle(stream):
 def even_moments(l_max: int):
     """(l, m) of the moment axis of B: even l, 0 <= m <= l."""
     return [(l, m) for l in range(0, l_max + 1, 2) for m in range(l + 1)]
+
+
+class Graph:
+    """A captured estimate (``estimator_graph_*``); keeps its tensors alive."""
+
+    def __init__(self, handle, keep):
+        self._h, self._keep = handle, keep
+
+    def launch(self, stream=None):
+        _check(load().estimator_graph_launch(self._h, _stream_handle(stream)), "estimator_graph_launch")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().estimator_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Plan:
@@ -160,6 +187,14 @@ class Plan:
         import torch
         return torch.empty(max(self.workspace_bytes(batch), 256), dtype=torch.uint8, device=device)
 
+    def _check_field(self, delta):
+        import torch
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if delta.dtype != want or not delta.is_cuda or not delta.is_contiguous():
+            raise ValueError(f"delta must be a contiguous CUDA {want} tensor")
+        if delta.dim() != 4 or tuple(delta.shape[1:]) != (self.n_g,) * 3:
+            raise ValueError("delta must be [batch][N][N][N] of the plan's grid size")
+
     def estimate(self, delta, workspace, out=None, stream=None):
         """delta: CUDA tensor [batch][N][N][N] (float32, or float64 for fp64);
         returns (or fills) a CUDA float64 tensor [batch][n_k1][n_mu][n_t][n_lm]."""
@@ -167,11 +202,7 @@ class Plan:
         if delta.dim() == 3:
             delta = delta.unsqueeze(0)
         batch = delta.shape[0]
-        want = torch.float64 if self.precision == "fp64" else torch.float32
-        if delta.dtype != want or not delta.is_cuda or not delta.is_contiguous():
-            raise ValueError(f"delta must be a contiguous CUDA {want} tensor")
-        if tuple(delta.shape[1:]) != (self.n_g,) * 3:
-            raise ValueError("delta has the wrong grid size")
+        self._check_field(delta)
         if out is None:
             out = torch.empty(self.out_shape(batch), dtype=torch.float64, device=delta.device)
         st = load().estimator_estimate(self._h, C.c_void_p(delta.data_ptr()), batch,
@@ -179,6 +210,17 @@ class Plan:
                                        _stream_handle(stream))
         _check(st, "estimator_estimate")
         return out
+
+    def graph(self, delta, workspace, out, stream=None) -> "Graph":
+        """Capture estimate(delta, workspace, out) into a CUDA graph
+        (``estimator_graph_create``); the tensors must outlive the graph."""
+        self._check_field(delta)
+        h = C.c_void_p()
+        st = load().estimator_graph_create(C.byref(h), self._h, C.c_void_p(delta.data_ptr()), delta.shape[0],
+                                           C.c_void_p(workspace.data_ptr()), C.c_void_p(out.data_ptr()),
+                                           _stream_handle(stream))
+        _check(st, "estimator_graph_create")
+        return Graph(h, (delta, workspace, out))
 
     def estimate_host(self, delta: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Host-memory variant: numpy in, numpy out (copies inside the call)."""

@@ -5,6 +5,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <new>
 #include <cstring>
 #include <string>
 #include <type_traits>
@@ -79,7 +81,10 @@ struct bisp_plan {
     RingArg ring_arg{};
     std::vector<Job *> d_jobs;           // per level in use
     std::vector<int64_t *> d_job_off;    // per level: output offsets of the jobs
-    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, ws_bytes = 0;
+    // one field's workspace region (offsets within it); field f of a batch
+    // uses bytes [f region_bytes, (f + 1) region_bytes) of the workspace
+    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, region_bytes = 0;
+    int last_field = 0;                  // field of the last estimate that introspection reads
     size_t resident = 0;
     // buffers of estimator_estimate_host
     void *own_ws = nullptr, *own_in = nullptr;
@@ -201,7 +206,7 @@ int check_desc(const bisp_desc *d)
     if (d->l_max < 0 || d->l_max > 8 || (d->l_max & 1)) return fail(BISP_INVALID_ARG, "l_max must be even, 0..8");
     if (d->precision < BISP_PREC_FP32 || d->precision > BISP_PREC_MIXED_TC)
         return fail(BISP_INVALID_ARG, "unknown precision");
-    if (d->max_batch < 1) return fail(BISP_INVALID_ARG, "max_batch must be >= 1");
+    if (d->max_batch < 1 || d->max_batch > 65535) return fail(BISP_INVALID_ARG, "max_batch must be in [1, 65535]");
     return BISP_OK;
 }
 
@@ -265,8 +270,9 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
             CK(cudaMemcpyAsync(d_jobs, jobs[lv].data(), jobs[lv].size() * sizeof(Job), cudaMemcpyHostToDevice, s));
             CK(cudaMemcpyAsync(d_joff, joff.data(), joff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
             CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lv].size()), M, true, gt,
-                                          p->tw_d, s));
-            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lv].size()), d_joff, 1.0, false, p->tw_d, s));
+                                          p->tw_d, Batch{}, s));
+            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lv].size()), d_joff, 1.0, false, p->tw_d,
+                                         Batch{}, s));
             CK(cudaStreamSynchronize(s));   // the job tables are reused by the next grid
         }
         CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), p->grid_arg, d_raw, s));
@@ -291,8 +297,24 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
     return st;
 }
 
+// Kernel attributes are per device; set them once per device in the process.
+int init_attributes()
+{
+    static std::mutex mu;
+    static std::vector<int> done;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(done.begin(), done.end(), dev) != done.end()) return BISP_OK;
+    CK(init_kernel_attributes());
+    CK(init_step2_tc_attributes());
+    done.push_back(dev);
+    return BISP_OK;
+}
+
 int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
 {
+    if (int st = init_attributes()) return st;
     HostPlan &P = p->hp;
     P.desc = *desc;
     P.k1_edges.assign(desc->k1_edges, desc->k1_edges + desc->n_k1 + 1);
@@ -382,7 +404,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
                                         cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = launch_epilogue<double>(1, p->d_rec, p->d_bin_start, P.n_bins, d_nt, desc->l_max, nullptr, 1.0,
-                                        p->d_den, s);
+                                        p->d_den, Batch{}, s);
         p->h_den.resize(size_t(P.n_bins) * P.n_lm);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->h_den.data(), p->d_den, p->h_den.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -420,7 +442,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->off_dstore = o; o = align256(o + size_t(P.dstore_elems) * p->celem);
     p->off_part = o; o = align256(o + size_t(P.n_partials) * sizeof(double));
     p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
-    p->ws_bytes = o;
+    p->region_bytes = o;
     CK(cudaStreamSynchronize(s));
     return BISP_OK;
 }
@@ -454,49 +476,53 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     double *Ssum = reinterpret_cast<double *>(ws + p->off_S);
     const int64_t ng2 = int64_t(ng) * ng;
     const R scale = R(P.volume / (double(ng2) * ng));
-    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk, part};
+    const int64_t fs = int64_t(p->region_bytes);          // between the fields' workspace regions
+    StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk, part, fs};
     TcArgs atc{p->d_tc_tiles, p->d_tc_rows, p->d_tc_slots, p->d_tc_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk,
-               part, p->d_status};
-    for (int b = 0; b < batch; ++b) {
-        const R *d = delta + int64_t(b) * ng2 * ng;
-        {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
-            StageMark m(p, BISP_STAGE_FORWARD, 3, s);
-            CK(launch_fft_z_real<R>(d, A_, ng, ng2, Rg.nz + 1, tw, s));
-            CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, s));
-            CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, s));
-        }
-        {   // Step I: D(r, n) on each reduction grid (Eq. iFT)
-            StageMark m(p, BISP_STAGE_STEP1, int(2 * P.levels.size()), s);
-            for (size_t l = 0; l < P.levels.size(); ++l) {
-                const Level &L = P.levels[l];
-                const int M = L.M;
-                CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, s));
-                CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, s));
-            }
-        }
-        {   // Step II: triple sums (Eq. fftbs)
-            StageMark m(p, BISP_STAGE_STEP2, step2_launches(P), s);
-            if constexpr (sizeof(R) == 4) {
-                if (P.tensor) {
-                    CK(launch_step2_tc(atc, dstore, P.tc_class_begin, s));
-                } else {
-                    CK(launch_step2<R>(a2, dstore, P.class_begin, s));
-                }
-            } else {
-                CK(launch_step2<R>(a2, dstore, P.class_begin, s));
-            }
-        }
-        {
-            StageMark m(p, BISP_STAGE_REDUCE, 1, s);
-            using RA = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
-            CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, s));
-        }
-        {   // binning and the ratio of Eq. bs_lm2_1
-            StageMark m(p, BISP_STAGE_BIN, 1, s);
-            CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
-                                  1.0 / (P.volume * double(ng2)), B + int64_t(b) * P.n_bins * P.n_lm, s));
+               part, p->d_status, fs};
+    // every stage runs once for all fields of the batch (gridDim.y = field)
+    const unsigned nf = unsigned(batch);
+    const Batch in_field{nf, int64_t(ng2) * ng * int64_t(sizeof(R)), fs};   // input field -> region
+    const Batch region{nf, fs, fs};
+    const Batch to_out{nf, fs, int64_t(P.n_bins) * P.n_lm * int64_t(sizeof(double))};
+    {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
+        StageMark m(p, BISP_STAGE_FORWARD, 3, s);
+        CK(launch_fft_z_real<R>(delta, A_, ng, ng2, Rg.nz + 1, tw, in_field, s));
+        CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, region, s));
+        CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, region, s));
+    }
+    {   // Step I: D(r, n) on each reduction grid (Eq. iFT)
+        StageMark m(p, BISP_STAGE_STEP1, int(2 * P.levels.size()), s);
+        for (size_t l = 0; l < P.levels.size(); ++l) {
+            const Level &L = P.levels[l];
+            const int M = L.M;
+            CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, region, s));
+            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, region, s));
         }
     }
+    {   // Step II: triple sums (Eq. fftbs)
+        StageMark m(p, BISP_STAGE_STEP2, step2_launches(P), s);
+        if constexpr (sizeof(R) == 4) {
+            if (P.tensor) {
+                CK(launch_step2_tc(atc, dstore, P.tc_class_begin, int(nf), s));
+            } else {
+                CK(launch_step2<R>(a2, dstore, P.class_begin, int(nf), s));
+            }
+        } else {
+            CK(launch_step2<R>(a2, dstore, P.class_begin, int(nf), s));
+        }
+    }
+    {
+        StageMark m(p, BISP_STAGE_REDUCE, 1, s);
+        using RA = typename std::conditional<std::is_same<S, float>::value, float, double>::type;
+        CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, region, s));
+    }
+    {   // binning and the ratio of Eq. bs_lm2_1
+        StageMark m(p, BISP_STAGE_BIN, 1, s);
+        CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
+                              1.0 / (P.volume * double(ng2)), B, to_out, s));
+    }
+    p->last_field = batch - 1;
     return BISP_OK;
 }
 
@@ -561,7 +587,7 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->n_items = int64_t(P.tensor ? P.tc_units.size() : P.units.size());
     info->triple_products = P.triple_products;
     info->dstore_bytes = size_t(P.dstore_elems) * p->celem;
-    info->workspace_bytes = p->ws_bytes;
+    info->workspace_bytes = p->region_bytes;
     info->resident_bytes = p->resident;
     return BISP_OK;
 }
@@ -569,7 +595,7 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
 size_t estimator_workspace_bytes(const bisp_plan *p, int batch)
 {
     if (!p || batch < 1 || batch > p->hp.desc.max_batch) return 0;
-    return p->ws_bytes;
+    return size_t(batch) * p->region_bytes;
 }
 
 int estimator_estimate(bisp_plan *p, const void *delta, int batch, void *workspace, double *B, void *stream)
@@ -592,7 +618,7 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
                          (p->precision == BISP_PREC_FP64 ? sizeof(double) : sizeof(float));
     const size_t outb = size_t(P.n_bins) * P.n_lm * sizeof(double);
     if (!p->own_ws) {
-        CK(cudaMalloc(&p->own_ws, std::max<size_t>(p->ws_bytes, 256)));
+        CK(cudaMalloc(&p->own_ws, std::max<size_t>(size_t(P.desc.max_batch) * p->region_bytes, 256)));
         CK(cudaMalloc(&p->own_in, field * P.desc.max_batch));
         CK(cudaMalloc((void **)&p->own_out, outb * P.desc.max_batch));
     }
@@ -601,6 +627,75 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
     if (st) return st;
     CK(cudaMemcpyAsync(B_host, p->own_out, outb * batch, cudaMemcpyDeviceToHost, s));
     return estimator_device_status(p, stream);
+}
+
+}  // extern "C"
+
+struct bisp_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t own = nullptr;
+};
+
+extern "C" {
+
+int estimator_graph_create(bisp_graph **out, bisp_plan *p, const void *delta, int batch, void *workspace,
+                           double *B, void *stream)
+{
+    g_err.clear();
+    if (!out) return fail(BISP_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !delta || !workspace || !B) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(BISP_INVALID_ARG, "workspace not 256-byte aligned");
+    bisp_graph *g = new (std::nothrow) bisp_graph();
+    if (!g) return fail(BISP_OUT_OF_MEMORY, "host allocation failed");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    auto bail = [&](int st) {
+        if (g->exec) cudaGraphExecDestroy(g->exec);
+        if (g->graph) cudaGraphDestroy(g->graph);
+        if (g->own) cudaStreamDestroy(g->own);
+        delete g;
+        cudaGetLastError();
+        return st;
+    };
+    if (!s) {
+        if (cudaStreamCreateWithFlags(&g->own, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(BISP_CUDA_ERROR, "stream for capture"));
+        s = g->own;
+    }
+    const bool timing = p->timing;
+    p->timing = false;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        p->timing = timing;
+        return bail(fail(BISP_CUDA_ERROR, std::string("begin capture: ") + cudaGetErrorString(e)));
+    }
+    const int st = dispatch_estimate(p, delta, batch, workspace, B, s);
+    e = cudaStreamEndCapture(s, &g->graph);
+    p->timing = timing;
+    if (st) return bail(st);
+    if (e != cudaSuccess) return bail(fail(BISP_CUDA_ERROR, std::string("end capture: ") + cudaGetErrorString(e)));
+    e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (e != cudaSuccess) return bail(fail(BISP_CUDA_ERROR, std::string("instantiate: ") + cudaGetErrorString(e)));
+    *out = g;
+    return BISP_OK;
+}
+
+int estimator_graph_launch(bisp_graph *g, void *stream)
+{
+    if (!g || !g->exec) return fail(BISP_INVALID_ARG, "NULL graph");
+    CK(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+    return BISP_OK;
+}
+
+void estimator_graph_destroy(bisp_graph *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->own) cudaStreamDestroy(g->own);
+    delete g;
 }
 
 int estimator_device_status(bisp_plan *p, void *stream)
@@ -713,7 +808,7 @@ int estimator_combo_sums(const bisp_plan *p, const void *workspace, double *S, v
 {
     if (!p || !workspace || !S) return fail(BISP_INVALID_ARG, "NULL argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    CK(cudaMemcpyAsync(S, static_cast<const unsigned char *>(workspace) + p->off_S,
+    CK(cudaMemcpyAsync(S, static_cast<const unsigned char *>(workspace) + size_t(p->last_field) * p->region_bytes + p->off_S,
                        size_t(p->hp.n_combos) * sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return BISP_OK;
@@ -744,7 +839,8 @@ int estimator_dfield(const bisp_plan *p, const void *workspace, int M, int n, in
         return fail(BISP_INVALID_ARG, "no such field");
     const int64_t o = P.doff[(size_t(lv) * (P.rings.nz + 1) + n) * kMaxRings + r];
     if (o < 0) return fail(BISP_INVALID_ARG, "field not stored on this grid");
-    const unsigned char *src = static_cast<const unsigned char *>(workspace) + p->off_dstore + size_t(o) * p->celem;
+    const unsigned char *src = static_cast<const unsigned char *>(workspace) + size_t(p->last_field) * p->region_bytes +
+                               p->off_dstore + size_t(o) * p->celem;
     return copy_complex_out(p, src, int64_t(M) * M, out, static_cast<cudaStream_t>(stream));
 }
 
@@ -754,7 +850,8 @@ int estimator_delta_plane(const bisp_plan *p, const void *workspace, int n, doub
     const HostPlan &P = p->hp;
     if (n < 0 || n > P.rings.nz) return fail(BISP_INVALID_ARG, "plane out of range");
     const int64_t ng2 = int64_t(P.desc.n_g) * P.desc.n_g;
-    const unsigned char *src = static_cast<const unsigned char *>(workspace) + p->off_a + size_t(n) * ng2 * p->celem;
+    const unsigned char *src = static_cast<const unsigned char *>(workspace) + size_t(p->last_field) * p->region_bytes +
+                               p->off_a + size_t(n) * ng2 * p->celem;
     return copy_complex_out(p, src, ng2, out, static_cast<cudaStream_t>(stream));
 }
 

@@ -43,6 +43,16 @@ template <typename C> __device__ __forceinline__ C cmk(double re, double im);
 template <> __device__ __forceinline__ float2 cmk<float2>(double re, double im) { return make_float2(float(re), float(im)); }
 template <> __device__ __forceinline__ double2 cmk<double2>(double re, double im) { return make_double2(re, im); }
 
+// Field f = blockIdx.y of a batched launch: its buffers sit fs bytes apart.
+template <typename T> __device__ __forceinline__ T *field_ptr(T *p, int64_t fs)
+{
+    return reinterpret_cast<T *>(reinterpret_cast<char *>(p) + int64_t(blockIdx.y) * fs);
+}
+template <typename T> __device__ __forceinline__ const T *field_ptr(const T *p, int64_t fs)
+{
+    return reinterpret_cast<const T *>(reinterpret_cast<const char *>(p) + int64_t(blockIdx.y) * fs);
+}
+
 // Stockham transform of nrows rows of length M = 2^q or 3 x 2^q held in
 // shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M): one
 // radix-3 stage first when 3 divides M, then radix-2 stages.  Every thread
@@ -104,10 +114,12 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M, int64_t rows,
-             int nkeep, int rt, Twiddles<typename Cx<R>::T> tw)
+             int nkeep, int rt, Twiddles<typename Cx<R>::T> tw, int64_t fs_in, int64_t fs_out)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    in = field_ptr(in, fs_in);
+    out = field_ptr(out, fs_out);
     const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
@@ -129,10 +141,12 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M,
              int nrow, int ntile, const int64_t *__restrict__ out_off, R scale, int zero_dc, int rt,
-             Twiddles<typename Cx<R>::T> tw)
+             Twiddles<typename Cx<R>::T> tw, int64_t fs)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    in = field_ptr(in, fs);
+    out = field_ptr(out, fs);
     const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
@@ -162,10 +176,12 @@ template <typename R, bool UNIT>
 __global__ void __launch_bounds__(256)
 k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg rings,
               const Job *__restrict__ jobs, int M, int ntile, int rt, typename Cx<R>::T *__restrict__ gt,
-              Twiddles<typename Cx<R>::T> tw)
+              Twiddles<typename Cx<R>::T> tw, int64_t fs)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    planes = field_ptr(planes, fs);
+    gt = field_ptr(gt, fs);
     const int P = M + 1;
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
@@ -238,6 +254,8 @@ template <typename R, int NW>
 __global__ void __launch_bounds__(32 * NW, (sizeof(R) == 8 ? 8 : 16) / NW)
 k_step2(StepIIArgs args, int64_t unit0, const typename Cx<R>::T *__restrict__ dstore, int smem_bytes)
 {
+    dstore = field_ptr(dstore, args.fs);
+    args.partials = field_ptr(args.partials, args.fs);
     using C = typename Cx<R>::T;
     constexpr int NT = 32 * NW;
     constexpr int PER16 = 16 / sizeof(C);     // complex values per 16-byte copy
@@ -367,8 +385,11 @@ k_step2(StepIIArgs args, int64_t unit0, const typename Cx<R>::T *__restrict__ ds
 
 template <typename A>
 __global__ void __launch_bounds__(256)
-k_reduce(const Group *__restrict__ groups, const double *__restrict__ partials, int ng, double *__restrict__ S)
+k_reduce(const Group *__restrict__ groups, const double *__restrict__ partials, int ng, double *__restrict__ S,
+         int64_t fs)
 {
+    partials = field_ptr(partials, fs);
+    S = field_ptr(S, fs);
     const Group G = groups[blockIdx.x];
     const double f = double(ng) / double(G.M);
     const A scale = A(f * f);
@@ -388,8 +409,10 @@ template <typename W, int LMAX>
 __global__ void __launch_bounds__(256)
 k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ bin_start, int64_t nbins,
            const double *__restrict__ value, const double *__restrict__ den, double norm,
-           double *__restrict__ out)
+           double *__restrict__ out, int64_t fs_in, int64_t fs_out)
 {
+    value = field_ptr(value, fs_in);
+    out = field_ptr(out, fs_out);
     constexpr int NLM = (LMAX / 2 + 1) * (LMAX / 2 + 1);
     const int64_t b = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
@@ -477,13 +500,6 @@ k_ntri(const double2 *__restrict__ I, const int64_t *__restrict__ ioff, const in
     }
 }
 
-template <typename F>
-cudaError_t set_smem(F f, size_t bytes)
-{
-    if (bytes > 48 * 1024) return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
-    return cudaSuccess;
-}
-
 }  // namespace
 
 size_t fft_rows_per_block(int M, size_t elem)
@@ -496,40 +512,37 @@ size_t fft_rows_per_block(int M, size_t elem)
 
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const int rt = int(fft_rows_per_block(ng, sizeof(C)));
     const size_t smem = size_t(2) * rt * (ng + 1) * sizeof(C);
-    cudaError_t e = set_smem(k_fft_z_real<R>, smem);
-    if (e != cudaSuccess) return e;
     const int64_t nblk = (rows + rt - 1) / rt;
-    k_fft_z_real<R><<<unsigned(nblk), 256, smem, s>>>(in, out, ng, rows, nkeep, rt, tw);
+    k_fft_z_real<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, ng, rows, nkeep, rt, tw, fb.fs_in,
+                                                                   fb.fs_out);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(nrow)));
     const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
-    cudaError_t e = set_smem(k_fft_rows_T<R>, smem);
-    if (e != cudaSuccess) return e;
     const int ntile = (nrow + rt - 1) / rt;
     const int64_t nblk = nb * ntile;
     if (nblk == 0) return cudaSuccess;
-    k_fft_rows_T<R><<<unsigned(nblk), 256, smem, s>>>(in, out, M, nrow, ntile, out_off, scale, zero_dc ? 1 : 0,
-                                                      rt, tw);
+    k_fft_rows_T<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, M, nrow, ntile, out_off, scale,
+                                                                   zero_dc ? 1 : 0, rt, tw, fb.fs_in);
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings, const Job *jobs,
                                int64_t njobs, int M, bool unit, typename Cx<R>::T *gt,
-                               const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s)
+                               const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(M)));
@@ -537,80 +550,100 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     const int ntile = (M + rt - 1) / rt;
     const int64_t nblk = njobs * ntile;
     if (nblk == 0) return cudaSuccess;
-    cudaError_t e;
-    if (unit) {
-        e = set_smem(k_ring_gather<R, true>, smem);
-        if (e != cudaSuccess) return e;
-        k_ring_gather<R, true><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw);
-    } else {
-        e = set_smem(k_ring_gather<R, false>, smem);
-        if (e != cudaSuccess) return e;
-        k_ring_gather<R, false><<<unsigned(nblk), 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw);
-    }
+    const dim3 grid(unsigned(nblk), fb.nf);
+    if (unit)
+        k_ring_gather<R, true><<<grid, 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw, fb.fs_in);
+    else
+        k_ring_gather<R, false><<<grid, 256, smem, s>>>(planes, ng, rings, jobs, M, ntile, rt, gt, tw, fb.fs_in);
     return cudaGetLastError();
 }
 
 template <typename R, int NW>
 cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t u0, int64_t n,
-                               size_t smem, cudaStream_t s)
+                               size_t smem, int nf, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    cudaError_t e = set_smem(k_step2<R, NW>, smem);
-    if (e != cudaSuccess) return e;
-    k_step2<R, NW><<<unsigned(n), 32 * NW, smem, s>>>(a, u0, dstore, int(smem));
+    k_step2<R, NW><<<dim3(unsigned(n), nf), 32 * NW, smem, s>>>(a, u0, dstore, int(smem));
     return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
-                         cudaStream_t s)
+                         int nf, cudaStream_t s)
 {
     if constexpr (sizeof(R) == 4) {
         cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                                 kStep2ClassSmem[2], s);
+                                                 kStep2ClassSmem[2], nf, s);
         if (e == cudaSuccess)
             e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                         kStep2ClassSmem[3], s);
+                                         kStep2ClassSmem[3], nf, s);
         if (e == cudaSuccess)
             e = launch_step2_class<R, 16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
-                                          kStep2ClassSmem[4], s);
+                                          kStep2ClassSmem[4], nf, s);
         return e;
     }
     // FP64: register tiles, blocks of at most 8 warps (register file)
     cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                             kStep2ClassSmem[2], s);
+                                             kStep2ClassSmem[2], nf, s);
     if (e == cudaSuccess)
         e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                     kStep2ClassSmem[3], s);
+                                     kStep2ClassSmem[3], nf, s);
     if (e == cudaSuccess && class_begin[5] != class_begin[4]) e = cudaErrorInvalidValue;
     return e;
 }
 
 template <typename A>
 cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const double *partials, int ng,
-                                   double *S, cudaStream_t s)
+                                   double *S, const Batch &fb, cudaStream_t s)
 {
     if (ngroups == 0) return cudaSuccess;
-    k_reduce<A><<<unsigned(ngroups), 256, 0, s>>>(groups, partials, ng, S);
+    k_reduce<A><<<dim3(unsigned(ngroups), fb.nf), 256, 0, s>>>(groups, partials, ng, S, fb.fs_in);
     return cudaGetLastError();
 }
 
 template <typename W>
 cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
                             const double *value, int l_max, const double *den, double norm, double *out,
-                            cudaStream_t s)
+                            const Batch &fb, cudaStream_t s)
 {
     if (nbins == 0) return cudaSuccess;
-    const unsigned nblk = unsigned((nbins * 32 + 255) / 256);
+    const dim3 grid(unsigned((nbins * 32 + 255) / 256), fb.nf);
+    const int64_t fi = fb.fs_in, fo = fb.fs_out;
     switch (l_max) {
-    case 0: k_epilogue<W, 0><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
-    case 2: k_epilogue<W, 2><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
-    case 4: k_epilogue<W, 4><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
-    case 6: k_epilogue<W, 6><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
-    case 8: k_epilogue<W, 8><<<nblk, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out); break;
+    case 0: k_epilogue<W, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 2: k_epilogue<W, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 4: k_epilogue<W, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 6: k_epilogue<W, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 8: k_epilogue<W, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Every kernel that takes more than 48 KB of dynamic shared memory is
+// allowed the 227 KB maximum once, up front, so that the launches of an
+// estimate are plain stream work (capturable in a CUDA graph).
+cudaError_t init_kernel_attributes()
+{
+    const int mx = 227 * 1024;
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    };
+    set((const void *)k_fft_z_real<float>);
+    set((const void *)k_fft_z_real<double>);
+    set((const void *)k_fft_rows_T<float>);
+    set((const void *)k_fft_rows_T<double>);
+    set((const void *)k_ring_gather<float, false>);
+    set((const void *)k_ring_gather<float, true>);
+    set((const void *)k_ring_gather<double, false>);
+    set((const void *)k_ring_gather<double, true>);
+    set((const void *)k_step2<float, 4>);
+    set((const void *)k_step2<float, 8>);
+    set((const void *)k_step2<float, 16>);
+    set((const void *)k_step2<double, 4>);
+    set((const void *)k_step2<double, 8>);
+    return e;
 }
 
 cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32_t *triples, int64_t ntriples,
@@ -629,17 +662,17 @@ cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cuda
 }
 
 // explicit instantiations
-template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const Twiddles<float2> &, cudaStream_t);
-template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const Twiddles<double2> &, cudaStream_t);
-template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const Twiddles<float2> &, cudaStream_t);
-template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, cudaStream_t);
-template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, cudaStream_t);
-template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, cudaStream_t);
-template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, cudaStream_t);
-template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, cudaStream_t);
-template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
-template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, cudaStream_t);
-template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, cudaStream_t);
-template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, cudaStream_t);
+template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const Twiddles<float2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const Twiddles<double2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const Twiddles<float2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, int, cudaStream_t);
+template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, int, cudaStream_t);
+template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
+template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
+template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t);
+template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t);
 
 }  // namespace bisp

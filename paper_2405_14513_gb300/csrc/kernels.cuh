@@ -35,6 +35,14 @@ struct GridArg {
     int M[kMaxLevels];
 };
 
+// Fields of a batched launch: gridDim.y = nf; field f reads its input fs_in
+// bytes and writes its output fs_out bytes past field f - 1's (kernels whose
+// buffers all lie in one per-field workspace region use fs_in for both).
+struct Batch {
+    unsigned nf = 1;
+    int64_t fs_in = 0, fs_out = 0;
+};
+
 // Step-I job: one (plane, ring) field on one reduction grid.
 struct Job {
     int32_t n, r;
@@ -50,6 +58,7 @@ struct StepIIArgs {
     int nr;                  // rings per plane
     int64_t x_chunk;         // grid points of one unit
     double *partials;
+    int64_t fs;              // bytes between the workspace regions of the fields of a batch
 };
 
 // --- launch helpers (kernels.cu); all return cudaGetLastError() --------------
@@ -58,7 +67,7 @@ struct StepIIArgs {
 // frequencies [0, nkeep) written transposed as out[k][row].
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s);
 
 // Batched row transforms written transposed: in[b][nrow][M] -> out[b][M][nrow]
 // (out at out_off[b] when out_off is not null, else b * M * nrow), times
@@ -66,7 +75,7 @@ cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const Twiddles<typename Cx<R>::T> &tw, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s);
 
 // Step I, first pass: ring r of plane n of Delta (planes [nz+1][ng][ng]),
 // folded onto the M x M grid, transformed along u_y, written transposed to
@@ -75,14 +84,14 @@ template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings,
                                const Job *jobs, int64_t njobs, int M, bool unit,
                                typename Cx<R>::T *gt, const Twiddles<typename Cx<R>::T> &tw,
-                               cudaStream_t s);
+                               const Batch &fb, cudaStream_t s);
 
 // Step II: partial triple sums of every unit, one block per unit, one launch
 // per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
 // 2^c warps with kStep2ClassSmem[c] bytes of shared memory).
 template <typename R>
 cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
-                         cudaStream_t s);
+                         int nf, cudaStream_t s);
 
 // Step II on tcgen05 (FP32 fields; step2_tc.cu).
 struct TcArgs {
@@ -95,23 +104,30 @@ struct TcArgs {
     int64_t x_chunk;
     double *partials;
     int *status;             // set to 1 by a block whose tensor-core wait ran out
+    int64_t fs;              // bytes between the workspace regions of the fields of a batch
 };
 
 // One launch per column class: units [class_begin[c], class_begin[c+1]),
 // one block per unit with kTcSmem bytes of shared memory.
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin, cudaStream_t s);
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin, int nf,
+                            cudaStream_t s);
+
+// Allow the kernels their dynamic shared memory once (kernels.cu and
+// step2_tc.cu), so that estimates are plain stream work.
+cudaError_t init_kernel_attributes();
+cudaError_t init_step2_tc_attributes();
 
 // S[c0 + j] = (ng/M)^2 sum_k partials[part0 + k ncombo + j]
 template <typename A>
 cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const double *partials,
-                                   int ng, double *S, cudaStream_t s);
+                                   int ng, double *S, const Batch &fb, cudaStream_t s);
 
 // Binning epilogue of Eq. bs_lm2_1.  mode 0: B = sqrt((2l+1)/4pi) num /
 // (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
 template <typename W>
 cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
                             const double *value, int l_max, const double *den, double norm,
-                            double *out, cudaStream_t s);
+                            double *out, const Batch &fb, cudaStream_t s);
 
 // Y_lm normalisations nlm[l][m] and the prefactors sqrt((2l+1)/(4 pi)).
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);

@@ -206,6 +206,9 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     const TcUnit U = args.units[unit0 + blockIdx.x];
     const TcTile T = args.tiles[U.tile];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    // field blockIdx.y of a batch: its D store and partial sums
+    dstore = reinterpret_cast<const float2 *>(reinterpret_cast<const char *>(dstore) + int64_t(blockIdx.y) * args.fs);
+    args.partials = reinterpret_cast<double *>(reinterpret_cast<char *>(args.partials) + int64_t(blockIdx.y) * args.fs);
     const int nslot = T.nslot, nf = nslot + NC;
     const int S = tc_stages(NC, nslot);          // ring depth (>= 3; the plan checked)
     const int rowb = (nf + 1) * kSlotBytes;      // one ring buffer: nf fields and a zero row
@@ -400,23 +403,30 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
 }
 
 template <int NC>
-cudaError_t launch_class(const TcArgs &a, const float2 *dstore, int64_t u0, int64_t n, cudaStream_t s)
+cudaError_t launch_class(const TcArgs &a, const float2 *dstore, int64_t u0, int64_t n, int nf, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_step2_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
-    if (e != cudaSuccess) return e;
-    k_step2_tc<NC><<<unsigned(n), kThreads, kTcSmem, s>>>(a, u0, dstore);
+    k_step2_tc<NC><<<dim3(unsigned(n), unsigned(nf)), kThreads, kTcSmem, s>>>(a, u0, dstore);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *cb, cudaStream_t s)
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *cb, int nf, cudaStream_t s)
 {
-    cudaError_t e = launch_class<16>(a, dstore, cb[0], cb[1] - cb[0], s);
-    if (e == cudaSuccess) e = launch_class<32>(a, dstore, cb[1], cb[2] - cb[1], s);
-    if (e == cudaSuccess) e = launch_class<48>(a, dstore, cb[2], cb[3] - cb[2], s);
-    if (e == cudaSuccess) e = launch_class<64>(a, dstore, cb[3], cb[4] - cb[3], s);
+    cudaError_t e = launch_class<16>(a, dstore, cb[0], cb[1] - cb[0], nf, s);
+    if (e == cudaSuccess) e = launch_class<32>(a, dstore, cb[1], cb[2] - cb[1], nf, s);
+    if (e == cudaSuccess) e = launch_class<48>(a, dstore, cb[2], cb[3] - cb[2], nf, s);
+    if (e == cudaSuccess) e = launch_class<64>(a, dstore, cb[3], cb[4] - cb[3], nf, s);
+    return e;
+}
+
+cudaError_t init_step2_tc_attributes()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_step2_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2_tc<48>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_step2_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTcSmem));
     return e;
 }
 

@@ -259,3 +259,49 @@ def test_tensor_core_full_size_512_sampled():
     scale = np.sqrt(np.mean(want ** 2))
     assert np.abs(S[pick] - want).max() < TOL["mixed_tc"] * scale
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Batched launches and captured estimates
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed", "fp64"])
+def test_batched_launch_equals_single_fields(precision):
+    """All fields of a batch go through each stage in one launch, each in its
+    own workspace region; every field's result must equal its own estimate."""
+    ng, L = 32, 500.0
+    edges = synth.default_k1_edges(ng, L, 3)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = api.Plan(ng, L, edges, 4, 4, 6, precision=precision, max_batch=3)
+    ws = plan.workspace(3)
+    fields = torch.stack([torch.from_numpy(synth.make_field(ng, L, s)) for s in (21, 22, 23)]).to(dt).cuda()
+    both = plan.estimate(fields.contiguous(), ws).cpu().numpy()
+    for i in range(3):
+        one = plan.estimate(fields[i:i + 1].contiguous(), ws).cpu().numpy()[0]
+        assert np.array_equal(both[i], one, equal_nan=True), i
+    assert plan.workspace_bytes(3) == 3 * plan.workspace_bytes(1)
+    plan.close()
+
+
+def test_captured_estimate_replays_exactly():
+    """estimator_graph_create captures a batched estimate; launching the graph
+    gives the estimate's result, and again after the inputs change in place."""
+    ng, L = 64, 1000.0
+    edges = synth.default_k1_edges(ng, L, 6)
+    plan = api.Plan(ng, L, edges, 5, 5, 6, precision="mixed_tc", max_batch=2)
+    ws = plan.workspace(2)
+    fields = torch.stack([torch.from_numpy(synth.make_field(ng, L, s).astype(np.float32)) for s in (31, 32)]).cuda()
+    want = plan.estimate(fields, ws).cpu().numpy()
+    out = torch.full(plan.out_shape(2), float("nan"), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    g = plan.graph(fields, ws, out, stream=side)
+    g.launch(stream=side)
+    side.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want, equal_nan=True)
+    fields[0].copy_(torch.from_numpy(synth.make_field(ng, L, 33).astype(np.float32)))
+    want2 = plan.estimate(fields, ws).cpu().numpy()
+    g.launch(stream=side)
+    side.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want2, equal_nan=True)
+    assert plan.device_status() == 0
+    g.close()
+    plan.close()
