@@ -26,6 +26,7 @@ workload, on the host cores, and prints the same JSON line.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -49,6 +50,8 @@ WORKLOADS = {
     # batched mocks: 256 seeded realisations, one plan, batches of 16 fields
     # per launch, each batch a captured CUDA graph
     "c4": {"ng": 128, "box": 500.0, "nk1": 12, "nmu": 10, "mocks": 256, "batch": 16},
+    # serving: a Poisson trace (20 requests/s) of mixed N_g, k1-bin runs and l_max
+    "c5": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 10, "requests": 300, "rate": 20.0},
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
@@ -462,6 +465,52 @@ def run_batched(args):
     return 0
 
 
+def run_serving(args):
+    """Serving (c5): the seeded 300-request Poisson trace through the serving
+    loop (resident plans, continuous batching on 4 streams, HBM budget), then
+    the same trace one request at a time on one stream (the plain
+    single-job form).  Latency = completion - arrival, queueing included."""
+    import torch
+
+    from paper_2405_14513_gb300 import serve
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    W = WORKLOADS[args.workload]
+    trace = serve.make_trace(W["requests"], rate=W["rate"], seed=0)
+    srv = serve.Server(precision=args.precision, budget_gb=160.0, streams=4)
+    warm = serve.make_trace(24, rate=200.0, seed=99)
+    srv.run(warm)
+    clocks = ClockSampler(index=local)
+    lat, span, _ = srv.run(trace)
+    clk = clocks.stop()
+    served = serve.summary(trace, lat, span)
+    batches = collections.Counter(k for _, k in srv.log)
+    srv.sched.slots = []
+    torch.cuda.empty_cache()
+    lat1, span1, _ = srv.run(trace, one_by_one=True)
+    single = serve.summary(trace, lat1, span1)
+    status = max(p.device_status() for p in srv.plans.values())
+    cfg = {"workload": "served estimator requests: Poisson arrivals 20/s, N_g in {64,128,256,512} "
+                       "(weights 0.4/0.3/0.2/0.1, L 1000/500/1000/2000 Mpc/h), runs of 4-30 of 30 default "
+                       "k1 bins, (mu,t) step 0.05, l_max in {2,4,6}; seeded trace of 300 requests",
+           "precision": f"{args.precision}: {PRECISION_TEXT[args.precision]}",
+           "server": "one resident plan per N_g (30 bins, l<=6; answers are slices); up to 16/8/4/1 "
+                     "fields per launch for N_g 64/128/256/512; 4 streams; 160 GB budget",
+           "field": "seeded synthetic, generated on the device per request (part of the latency)"}
+    line = {"metric": "served B_l^m configs/s and p50/p99 latency (s)", "value": served["configs_per_s"],
+            "unit": "configs/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": span * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg, "served": served, "one_by_one": single,
+            "served_over_one_by_one": served["configs_per_s"] / single["configs_per_s"],
+            "launch_batch_sizes": dict(sorted(batches.items())), "device_status": status, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    srv.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -470,7 +519,7 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
                     help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, "
-                         "6 bins; c4: 256 mocks of 128^3 in batched graphs")
+                         "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
                     help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
@@ -479,6 +528,8 @@ def main(argv=None):
         return run_reference(args)
     if "mocks" in WORKLOADS[args.workload]:
         return run_batched(args)
+    if "requests" in WORKLOADS[args.workload]:
+        return run_serving(args)
     return run_ours(args)
 
 
