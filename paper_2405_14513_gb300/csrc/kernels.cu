@@ -404,6 +404,8 @@ k_reduce(const Group *__restrict__ groups, const double *__restrict__ partials, 
 // sqrt((2l+1)/(4 pi)) of Eq. bs_lm2_1, set by set_ylm_constants.
 __constant__ double c_nlm[9][9];
 __constant__ double c_pref[9];
+// Legendre recurrence ratios (2l+1)/(l+1-m) and (l+m)/(l+1-m), l, m <= 8
+__constant__ double c_rec[2][9][9];
 
 template <typename W, int LMAX>
 __global__ void __launch_bounds__(256)
@@ -449,7 +451,9 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
                         acc[idx] += y * y * v;
                     }
                 }
-                const W pn = (W(2 * l + 1) * x * pl - W(l + m) * plm1) / W(l + 1 - m);
+                // P_{l+1}^m = ((2l+1) x P_l^m - (l+m) P_{l-1}^m) / (l+1-m), with
+                // the two ratios from constant memory (no division per record)
+                const W pn = W(c_rec[0][l][m]) * x * pl - W(c_rec[1][l][m]) * plm1;
                 plm1 = pl;
                 pl = pn;
             }
@@ -656,9 +660,17 @@ cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32
 
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s)
 {
+    double rec[2][9][9] = {};
+    for (int l = 0; l <= 8; ++l)
+        for (int m = 0; m <= l; ++m) {
+            rec[0][l][m] = double(2 * l + 1) / double(l + 1 - m);
+            rec[1][l][m] = double(l + m) / double(l + 1 - m);
+        }
     cudaError_t e = cudaMemcpyToSymbolAsync(c_nlm, nlm, sizeof(double) * 81, 0, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return e;
-    return cudaMemcpyToSymbolAsync(c_pref, pref, sizeof(double) * 9, 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_pref, pref, sizeof(double) * 9, 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_rec, rec, sizeof(rec), 0, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the tables above live on this stack
+    return e;
 }
 
 // explicit instantiations

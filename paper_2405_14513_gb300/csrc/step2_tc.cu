@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kTX = kTcTX;                   // grid points per stage (K = 32)
 constexpr int kSlotBytes = kTcSlotBytes;
-constexpr uint32_t kTmemCols = 256;          // A[2]: hi 32 + lo 32 columns each; two accumulators of 64
+constexpr uint32_t kTmemCols = 256;          // A[2] (hi 32 + lo 32 columns each), then the accumulators
 constexpr int kWaitSpins = 1 << 22;          // bound of a tensor-core completion wait
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -108,23 +108,26 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NC])
 //   warps 0-3  form A (one row per thread = tensor-memory lane), write B's
 //              high and low parts, and add each stage's accumulators into
 //              FP32 registers;
-//   warps 4-5  (one thread each) issue the MMAs of a stage, six each, into
-//              two accumulators: a tcgen05.mma holds its issuing thread for
-//              tens of cycles, so two issuers per block keep the tensor
-//              cores fed;
+//   warps 4-5  (one thread each) issue the MMAs: a tcgen05.mma holds its
+//              issuing thread for tens of cycles, so for NC <= 32 two
+//              issuers split the 12 MMAs of a stage, each into its own
+//              accumulator (tensor-memory columns 128 + 64 b + 32 i for
+//              stage buffer b, issuer i); for NC > 32 warp 4 issues all 12
+//              into columns 128 + 64 b.  Accumulators are double-buffered,
+//              so the MMAs of stage s wait only for stage s - 2's read;
 //   warps 6-7  stage the fields of each stage in shared memory (cp.async,
 //              a ring of 3 to 8 stages).
 // mbarriers (phase k of a barrier = its k-th use):
 //   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
 //   empty[q]  ring buffer q has been read             (128 compute arrivals)
 //   aready[b] A and B (high, low) of buffer b written (128 compute arrivals)
-//   mdone[i]  the MMAs of issuer i's stage are done   (commit)
-//   dfree     both accumulators have been read        (128 compute arrivals)
+//   mdone[b][i] issuer i's MMAs into buffer b are done (commit)
+//   dfree[b]  accumulators of buffer b have been read (128 compute arrivals)
 constexpr int kThreads = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
-    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2], dfree;
+    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2][2], dfree[2];
     uint32_t tmem;
     int abort;
 };
@@ -201,6 +204,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     constexpr uint32_t SBO = 128;                // next 8 rows of B
     constexpr int BB = NC * kTX * 8;             // bytes of one stage of B
     constexpr uint32_t ID = idesc_tf32<NC>();
+    constexpr bool kTwoIssuers = NC <= 32;       // two accumulators of 32 columns fit a buffer
     extern __shared__ __align__(1024) unsigned char smem[];
 
     const TcUnit U = args.units[unit0 + blockIdx.x];
@@ -239,9 +243,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sy->aready[b], 128);
-            mbar_init(&sy->mdone[b], 1);
+            mbar_init(&sy->mdone[b][0], 1);
+            mbar_init(&sy->mdone[b][1], 1);
+            mbar_init(&sy->dfree[b], 128);
         }
-        mbar_init(&sy->dfree, 128);
         sy->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -295,35 +300,38 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else if (warp >= 4) {
-        // MMA issue.  Issuer 0: high A x high B over k-steps 0-3, low A x
-        // high B over k-steps 0-1; issuer 1: low A x high B over 2-3, high A
-        // x low B over 0-3; each into its own accumulator.
+        // MMA issue.  NC <= 32: issuer 0 takes high A x high B over k-steps
+        // 0-3 and low A x high B over 0-1, issuer 1 low A x high B over 2-3
+        // and high A x low B over 0-3.  NC > 32: issuer 0 takes all 12.
         const int me = warp - 4;
-        if (lane == 0) {
+        if (lane == 0 && (kTwoIssuers || me == 0)) {
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
-            const uint32_t d = tmem + 128 + 64 * me;
             for (int st = 0; st < nstage && ok; ++st) {
                 const int b = st & 1;
                 ok = mbar_wait_abort(&sy->aready[b], uint32_t(st >> 1) & 1, abort);
-                if (ok && st >= 1) ok = mbar_wait_abort(&sy->dfree, uint32_t(st - 1) & 1, abort);
+                if (ok && st >= 2) ok = mbar_wait_abort(&sy->dfree[b], uint32_t((st - 2) >> 1) & 1, abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a = tmem + 64 * b;
+                const uint32_t d = tmem + 128 + 64 * b + (kTwoIssuers ? 32 * me : 0);
                 const uint64_t bo = uint64_t(b * BB) >> 4;      // start-address field offset of buffer b
                 constexpr uint64_t kstep = (2 * LBO) >> 4;      // next k-step (two core matrices along K)
                 if (me == 0) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dh + bo + j * kstep, ID, j > 0);
 #pragma unroll
-                    for (int j = 0; j < 2; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
-                } else {
+                    for (int j = 0; j < (kTwoIssuers ? 2 : 4); ++j)
+                        mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
+                }
+                if (me == 1 || !kTwoIssuers) {
 #pragma unroll
-                    for (int j = 2; j < 4; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, j > 2);
+                    for (int j = (kTwoIssuers ? 2 : 4); j < 4; ++j)
+                        mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, j > 2);
 #pragma unroll
                     for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dl + bo + j * kstep, ID, 1);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                             ::"r"(su32(&sy->mdone[me])) : "memory");
+                             ::"r"(su32(&sy->mdone[b][me])) : "memory");
             }
         }
         __syncwarp();
@@ -372,15 +380,17 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 mbar_arrive(&sy->aready[b]);
             }
             if (st > 0) {
-                // accumulators of stage st - 1
-                const uint32_t par = uint32_t(st - 1) & 1;
-                ok = mbar_wait_abort(&sy->mdone[0], par, abort) && mbar_wait_abort(&sy->mdone[1], par, abort);
+                // accumulators of stage st - 1 (buffer b)
+                const int b = (st - 1) & 1;
+                const uint32_t par = uint32_t((st - 1) >> 1) & 1;
+                ok = mbar_wait_abort(&sy->mdone[b][0], par, abort) &&
+                     (!kTwoIssuers || mbar_wait_abort(&sy->mdone[b][1], par, abort));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                add_accumulator<NC>(tlane + 128, acc);
-                add_accumulator<NC>(tlane + 192, acc);
+                add_accumulator<NC>(tlane + 128 + 64 * b, acc);
+                if (kTwoIssuers) add_accumulator<NC>(tlane + 128 + 64 * b + 32, acc);
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(&sy->dfree);
+                mbar_arrive(&sy->dfree[b]);
             }
         }
         if (live) {
