@@ -134,9 +134,30 @@ static void fft_radix2(cplx *x, int n)
     }
 }
 
+/* n = 3 m, m a power of two: the sum over j split by j mod 3,
+ * X_k = sum_{q=0..2} exp(-2 pi i q k / n) F_q(k mod m), F_q the m-point DFT
+ * of x_{3j+q}. */
+static void fft_radix3_2(cplx *x, int n, cplx *tmp)
+{
+    const int m = n / 3;
+    for (int q = 0; q < 3; ++q) {
+        for (int j = 0; j < m; ++j) tmp[q * m + j] = x[3 * j + q];
+        fft_radix2(tmp + q * m, m);
+    }
+    for (int k = 0; k < n; ++k) {
+        cplx s = tmp[k % m];
+        for (int q = 1; q < 3; ++q) {
+            double a = -BO_TWO_PI * (double)((q * k) % n) / (double)n;
+            s += (cos(a) + I * sin(a)) * tmp[q * m + k % m];
+        }
+        x[k] = s;
+    }
+}
+
 static void dft1(cplx *x, int n, cplx *tmp)
 {
     if (is_pow2(n)) fft_radix2(x, n);
+    else if (n % 3 == 0 && is_pow2(n / 3)) fft_radix3_2(x, n, tmp);
     else dft_definition(x, n, tmp);
 }
 
