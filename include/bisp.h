@@ -47,7 +47,7 @@ extern "C" {
 typedef enum {
     BISP_OK = 0,
     BISP_INVALID_ARG = 1,       /* a parameter is out of range or inconsistent */
-    BISP_UNSUPPORTED_SIZE = 2,  /* N_g is not a power of two in [8, 1024]     */
+    BISP_UNSUPPORTED_SIZE = 2,  /* N_g is not 2^k or 3 x 2^k in [8, 1024]     */
     BISP_OUT_OF_MEMORY = 3,     /* a device or host allocation failed         */
     BISP_CUDA_ERROR = 4,        /* a CUDA call or kernel launch failed        */
     BISP_TIMEOUT = 5,           /* a bounded device wait gave up              */
@@ -68,7 +68,7 @@ typedef enum {
 typedef struct bisp_plan bisp_plan;
 
 typedef struct {
-    int n_g;                  /* grid points per side, power of two, 8..1024      */
+    int n_g;                  /* grid points per side, 2^k or 3 x 2^k, 8..1024    */
     double box_len;           /* L > 0; V = L^3, k_f = 2 pi / L                   */
     int n_k1;                 /* number of k1 bins, >= 1                          */
     const double *k1_edges;   /* HOST pointer, n_k1 + 1 strictly ascending edges, */

@@ -191,8 +191,8 @@ void free_plan(bisp_plan *p)
 int check_desc(const bisp_desc *d)
 {
     if (!d) return fail(BISP_INVALID_ARG, "desc is NULL");
-    if (d->n_g < 8 || d->n_g > 1024 || (d->n_g & (d->n_g - 1)))
-        return fail(BISP_UNSUPPORTED_SIZE, "n_g must be a power of two in [8, 1024]");
+    if (!grid_size_supported(d->n_g))
+        return fail(BISP_UNSUPPORTED_SIZE, "n_g must be 2^k or 3 x 2^k in [8, 1024]");
     if (!(d->box_len > 0) || !std::isfinite(d->box_len)) return fail(BISP_INVALID_ARG, "box_len must be > 0");
     if (d->n_k1 < 1 || !d->k1_edges) return fail(BISP_INVALID_ARG, "need n_k1 >= 1 and k1_edges");
     for (int b = 0; b < d->n_k1; ++b)
@@ -335,7 +335,13 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     // twiddles in double: exp(-2 pi i k / N_g), k < N_g / 2, for the lengths
     // 2^q, and exp(-2 pi i k / (3 N_g / 2)), k < 3 N_g / 4, for 3 x 2^q
     {
-        const int lg2 = ilog2i(desc->n_g);
+        // lengths 2^q <= N_g use exp(-2 pi i k / 2^lg2); lengths 3 x 2^q <= N_g
+        // use exp(-2 pi i k / (3 x 2^lg3))
+        const int ng = desc->n_g;
+        int lg2 = 0, lg3 = 0;
+        while ((2 << lg2) <= ng) ++lg2;
+        while (3 * (2 << lg3) <= ng) ++lg3;
+        if (lg3 < 1) lg3 = 1;
         auto table = [&](int base, int count, float2 **df, double2 **dd) -> int {
             std::vector<double2> twd(count);
             std::vector<float2> twf(count);
@@ -349,11 +355,11 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
         };
         float2 *f2 = nullptr, *f3 = nullptr;
         double2 *d2 = nullptr, *d3 = nullptr;
-        int st = table(desc->n_g, desc->n_g / 2, &f2, &d2);
-        if (!st) st = table(3 * desc->n_g / 2, 3 * desc->n_g / 4, &f3, &d3);
+        int st = table(1 << lg2, 1 << (lg2 - 1), &f2, &d2);
+        if (!st) st = table(3 << lg3, 3 << (lg3 - 1), &f3, &d3);
         if (st) return st;
-        p->tw_f = Twiddles<float2>{f2, f3, lg2, lg2 - 1};
-        p->tw_d = Twiddles<double2>{d2, d3, lg2, lg2 - 1};
+        p->tw_f = Twiddles<float2>{f2, f3, lg2, lg3};
+        p->tw_d = Twiddles<double2>{d2, d3, lg2, lg3};
     }
     // Y_lm normalisations
     {

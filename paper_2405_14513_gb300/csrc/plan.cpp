@@ -13,9 +13,16 @@
 
 namespace bisp {
 
+bool grid_size_supported(int ng)
+{
+    if (ng < 8 || ng > 1024) return false;
+    const int m = ng % 3 == 0 ? ng / 3 : ng;
+    return (m & (m - 1)) == 0;
+}
+
 bool build_rings(int ng, Rings &R)
 {
-    if (ng < 8 || ng > 1024 || (ng & (ng - 1))) return false;
+    if (!grid_size_supported(ng)) return false;
     R = Rings{};
     R.ng = ng;
     R.nz = ng / 3;

@@ -214,6 +214,9 @@ struct HostPlan {
     int64_t gt_elems = 0;               // largest per-level Step-I scratch
 };
 
+// N_g = 2^k or 3 x 2^k in [8, 1024] (the transform lengths the kernels handle).
+bool grid_size_supported(int ng);
+
 // Build the ring table; returns false for an unsupported N_g.
 bool build_rings(int ng, Rings &R);
 

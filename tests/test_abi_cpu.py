@@ -35,8 +35,9 @@ def test_status_strings():
 
 
 @pytest.mark.parametrize("kw,code", [
-    (dict(n_g=48), 2),
+    (dict(n_g=40), 2),
     (dict(n_g=4), 2),
+    (dict(n_g=1536), 2),
     (dict(n_g=2048), 2),
     (dict(l_max=3), 1),
     (dict(l_max=10), 1),

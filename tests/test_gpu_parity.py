@@ -305,3 +305,39 @@ def test_captured_estimate_replays_exactly():
     assert plan.device_status() == 0
     g.close()
     plan.close()
+
+
+# --------------------------------------------------------------------------
+# Grids of 3 x 2^k points (the paper's N_g = 384 study)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["mixed_tc", "fp64"])
+def test_grid_of_3_times_2k_matches_oracle(precision):
+    """N_g = 48 = 3 x 16: every transform length has a radix-3 stage."""
+    c = Case(48, 700.0, 4, 5, 5, 6, precision=precision, seed=17)
+    ref = O.select_even(c.oracle["B"], c.l_max)
+    assert floored_rel_err(c.B, ref).max() < TOL[precision]
+
+
+def test_grid_384_sampled_sums():
+    """N_g = 384, L = 215 (the paper's validation grid): Re S of sampled
+    combinations on every reduction grid against the oracle."""
+    ng, L = 384, 215.0
+    kf = 2 * np.pi / L
+    edges = np.array([2.0, 2.2])                      # k1 = 2.1 +- 0.1
+    assert edges[-1] <= ng / 3 * kf
+    plan = api.Plan(ng, L, edges, 10, 10, 6, precision="mixed_tc")
+    ws = plan.workspace(1)
+    fd = synth.make_field_torch(ng, L, 3, beta=1.0, device="cuda").float().contiguous()
+    field = fd.cpu().numpy()
+    plan.estimate(fd[None], ws)
+    assert plan.device_status() == 0
+    tab = plan.combo_table()
+    S = plan.combo_sums(ws)
+    rng = np.random.default_rng(19)
+    pick = []
+    for M in np.unique(tab["grid"]):
+        idx = np.flatnonzero(tab["grid"] == M)
+        pick.extend(rng.choice(idx, size=min(4, len(idx)), replace=False))
+    want = O.combo_sums(field.astype(np.float64), L, tab["ints"][np.array(pick)]).real
+    assert np.abs(S[np.array(pick)] - want).max() < TOL["mixed_tc"] * np.sqrt(np.mean(want ** 2))
+    plan.close()
