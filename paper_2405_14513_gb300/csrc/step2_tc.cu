@@ -80,50 +80,52 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
                    "r"(v[7]) : "memory");
 }
 
-// 16 columns of this thread's lane; the wait is in the same statement so the
-// registers are not read before the load completes.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+// The loads below keep the wait in the same statement, so the registers are
+// not read before the load completes.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
                  "tcgen05.wait::ld.sync.aligned;\n"
-                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                   "=r"(v[15])
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
                  : "r"(taddr) : "memory");
 }
 
-template <int NC>
-__device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NC])
+// acc[j] += accumulator column tcol + j, j < NH (NH a multiple of 8)
+template <int NH>
+__device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 {
 #pragma unroll
-    for (int q = 0; q < NC / 16; ++q) {
-        uint32_t v[16];
-        tmem_ld16(tcol + 16 * q, v);
+    for (int q = 0; q < NH / 8; ++q) {
+        uint32_t v[8];
+        tmem_ld8(tcol + 8 * q, v);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[16 * q + j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 8; ++j) acc[8 * q + j] += __uint_as_float(v[j]);
     }
 }
 
 // One block per unit (tile, x chunk), warp-specialised:
-//   warps 0-3  form A (one row per thread = tensor-memory lane), write B's
-//              high and low parts, and add each stage's accumulators into
-//              FP32 registers;
-//   warps 4-5  (one thread each) issue the MMAs: a tcgen05.mma holds its
+//   warps 0-7  form A and write B's high and low parts; warps w and w + 4
+//              share tensor-memory lanes 32 (w % 4) .. (the tile's rows,
+//              one per lane): warp w forms grid points 0-7 of a stage and
+//              adds accumulator columns 0 .. NC/2 - 1 into FP32 registers,
+//              warp w + 4 points 8-15 and columns NC/2 .. NC - 1;
+//   warps 8-9  (one thread each) issue the MMAs: a tcgen05.mma holds its
 //              issuing thread for tens of cycles, so for NC <= 32 two
 //              issuers split the 12 MMAs of a stage, each into its own
 //              accumulator (tensor-memory columns 128 + 64 b + 32 i for
 //              stage buffer b, issuer i); for NC > 32 warp 4 issues all 12
 //              into columns 128 + 64 b.  Accumulators are double-buffered,
 //              so the MMAs of stage s wait only for stage s - 2's read;
-//   warps 6-7  stage the fields of each stage in shared memory (cp.async,
+//   warps 10-11 stage the fields of each stage in shared memory (cp.async,
 //              a ring of 3 to 8 stages).
 // mbarriers (phase k of a barrier = its k-th use):
 //   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
-//   empty[q]  ring buffer q has been read             (128 compute arrivals)
-//   aready[b] A and B (high, low) of buffer b written (128 compute arrivals)
+//   empty[q]  ring buffer q has been read             (256 compute arrivals)
+//   aready[b] A and B (high, low) of buffer b written (256 compute arrivals)
 //   mdone[b][i] issuer i's MMAs into buffer b are done (commit)
-//   dfree[b]  accumulators of buffer b have been read (128 compute arrivals)
-constexpr int kThreads = 256;
+//   dfree[b]  accumulators of buffer b have been read (256 compute arrivals)
+constexpr int kThreads = 384;
+constexpr int kCompute = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
@@ -159,12 +161,13 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, vo
     return false;
 }
 
-// The A columns of one stage for this thread's row: P = D1' D2' with
-// D' the stored field or its conjugate (G1, G2: n1 < 0, n2 < 0), and
-// A = (Re P, -g3 Im P) (G3: n3 < 0), high parts at column a, low parts at
-// a + 32.  u8, v8: the row's two staged fields (16 points each).
+// The A columns of half a stage (grid points 8 half .. 8 half + 7) for this
+// thread's row: P = D1' D2' with D' the stored field or its conjugate (G1,
+// G2: n1 < 0, n2 < 0), and A = (Re P, -g3 Im P) (G3: n3 < 0), high parts at
+// column a + 16 half, low parts at a + 32 + 16 half.  u8, v8: the row's two
+// staged fields (16 points each).
 template <bool G1, bool G2, bool G3>
-__device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned char *v8, uint32_t a)
+__device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned char *v8, uint32_t a, int half)
 {
     // Re P = ux vx - g1 g2 uy vy;  -g3 Im P = s2 ux vy + s1 uy vx,
     // s2 = -g3 g2, s1 = -g3 g1
@@ -172,7 +175,8 @@ __device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned c
     constexpr bool NEG2 = !(G3 ^ G2);             // s2 = -1
     constexpr bool NEG1 = !(G3 ^ G1);             // s1 = -1
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {                 // 4 grid points = 8 columns
+    for (int hh = 0; hh < 2; ++hh) {              // 4 grid points = 8 columns
+        const int h = 2 * half + hh;
         uint32_t hi[8], lo[8];
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -239,13 +243,13 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     if (t == 0) {
         for (int q = 0; q < S; ++q) {
             mbar_init(&sy->full[q], 64);
-            mbar_init(&sy->empty[q], 128);
+            mbar_init(&sy->empty[q], kCompute);
         }
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&sy->aready[b], 128);
+            mbar_init(&sy->aready[b], kCompute);
             mbar_init(&sy->mdone[b][0], 1);
             mbar_init(&sy->mdone[b][1], 1);
-            mbar_init(&sy->dfree[b], 128);
+            mbar_init(&sy->dfree[b], kCompute);
         }
         sy->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -274,12 +278,12 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     const int nstage = int((x1 - x0) / kTX);
     bool ok = true;
 
-    if (warp >= 6) {
+    if (warp >= 10) {
         // producers: lane l of the 64 copies piece p = l % 8 (grid points
         // 2p, 2p + 1) of fields l / 8, l / 8 + 8, ...; their offsets (in
         // 16-element units: every stored field starts at a multiple of 16)
         // are held in registers
-        const int pl = t - 192, p = pl & 7, f0 = pl >> 3;
+        const int pl = t - 320, p = pl & 7, f0 = pl >> 3;
         uint32_t o16[kProdFields];
 #pragma unroll
         for (int k = 0; k < kProdFields; ++k) {
@@ -299,11 +303,11 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(&sy->full[q])) : "memory");
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-    } else if (warp >= 4) {
+    } else if (warp >= 8) {
         // MMA issue.  NC <= 32: issuer 0 takes high A x high B over k-steps
         // 0-3 and low A x high B over 0-1, issuer 1 low A x high B over 2-3
         // and high A x low B over 0-3.  NC > 32: issuer 0 takes all 12.
-        const int me = warp - 4;
+        const int me = warp - 8;
         if (lane == 0 && (kTwoIssuers || me == 0)) {
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
             for (int st = 0; st < nstage && ok; ++st) {
@@ -336,16 +340,19 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         }
         __syncwarp();
     } else {
-        // compute warps: thread t owns tensor-memory lane t (row t of the tile);
-        // rows past the tile's end read the zero row
-        const bool live = t < T.nrow;
+        // compute warps: the thread owns tensor-memory lane (row) 32 (warp % 4)
+        // + lane; rows past the tile's end read the zero row
+        constexpr int NH = NC / 2;               // accumulator columns of this thread
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = quarter * 32 + lane;
+        const bool live = row < T.nrow;
         TcRow R{};
-        if (live) R = args.rows[T.row0 + t];
+        if (live) R = args.rows[T.row0 + row];
         const int s1 = live ? R.s1 : nf, s2 = live ? R.s2 : nf;
-        const uint32_t tlane = tmem + (uint32_t(warp * 32) << 16);
-        float acc[NC];
+        const uint32_t tlane = tmem + (uint32_t(quarter * 32) << 16);
+        float acc[NH];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] = 0.f;
+        for (int c = 0; c < NH; ++c) acc[c] = 0.f;
         for (int st = 0; st <= nstage && ok; ++st) {
             if (st < nstage) {
                 const int q = st % S, b = st & 1;
@@ -357,7 +364,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 // rows 8 (c / 8) ..), row c % 8.  Buffer b was last read by the
                 // MMAs of stage st - 2, complete: their accumulators were read
                 // at stage st - 1.
-                for (int i = t; i < NC * 8; i += 128) {
+                for (int i = t; i < NC * 8; i += kCompute) {
                     const int c = i % NC, p = i / NC;
                     const float4 v = *reinterpret_cast<const float4 *>(sq + (nslot + c) * kSlotBytes + p * 16);
                     const int o = b * BB + (p * NB + c / 8) * 128 + (c % 8) * 16;
@@ -368,10 +375,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
                 const uint32_t a = tlane + 64 * b;
                 switch (T.flags) {   // uniform over the tile; n1 >= 0 (half space)
-                case 0: form_a<false, false, false>(u8, v8, a); break;
-                case 2: form_a<false, true, false>(u8, v8, a); break;
-                case 4: form_a<false, false, true>(u8, v8, a); break;
-                default: form_a<false, true, true>(u8, v8, a); break;
+                case 0: form_a<false, false, false>(u8, v8, a, half); break;
+                case 2: form_a<false, true, false>(u8, v8, a, half); break;
+                case 4: form_a<false, false, true>(u8, v8, a, half); break;
+                default: form_a<false, true, true>(u8, v8, a, half); break;
                 }
                 mbar_arrive(&sy->empty[q]);
                 asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
@@ -387,8 +394,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                      (!kTwoIssuers || mbar_wait_abort(&sy->mdone[b][1], par, abort));
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                add_accumulator<NC>(tlane + 128 + 64 * b, acc);
-                if (kTwoIssuers) add_accumulator<NC>(tlane + 128 + 64 * b + 32, acc);
+                add_accumulator<NH>(tlane + 128 + 64 * b + NH * half, acc);
+                if (kTwoIssuers) add_accumulator<NH>(tlane + 128 + 64 * b + 32 + NH * half, acc);
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 mbar_arrive(&sy->dfree[b]);
             }
@@ -397,8 +404,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             double *dst = args.partials + R.p0 + int64_t(U.chunk) * R.stride;
             const double nan = __longlong_as_double(0x7FF8000000000000LL);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const int j = c - int(R.col0);
+            for (int c = 0; c < NH; ++c) {
+                const int j = c + NH * half - int(R.col0);
                 if (j >= 0 && j < int(R.n)) dst[j] = ok ? double(acc[c]) : nan;
             }
         }
