@@ -168,9 +168,10 @@ const char *estimator_last_error(void);
 /* ---------------- estimate without caller-provided workspace ---------------- */
 
 /* estimator_estimate for callers that cannot allocate device memory: code
- * running while a stream is captured into a CUDA graph, code under a memory
- * manager that owns the device heap, plugins given a device and a stream but
- * no allocator.  (The paper has no counterpart: this is a deployment entry
+ * under a memory manager that owns the whole device heap (a framework's
+ * caching allocator, a serving runtime with fixed pools) and must not see
+ * stray allocations, and plugins handed a device and a stream but no
+ * allocator.  (The paper has no counterpart: this is a deployment entry
  * point.)
  *   delta, batch, B, stream: as for estimator_estimate (DEVICE pointers);
  *   the workspace is a file-scope device array of the library,

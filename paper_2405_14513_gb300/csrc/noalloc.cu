@@ -2,13 +2,12 @@
 // with its workspace in a file-scope device array instead of caller memory.
 //
 // Some callers cannot allocate device memory at the point where they run the
-// estimate: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not allowed during capture), code under a memory manager that
-// owns the whole device heap (a framework caching allocator, an MPI or
-// serving runtime that hands out fixed pools) and must not see stray
-// allocations, or plugins that are given a device and a stream but no
-// allocator.  For plans small enough, this entry point needs nothing from the
-// caller but the input field and the output array.
+// estimate: code under a memory manager that owns the whole device heap (a
+// framework caching allocator, an MPI or serving runtime that hands out fixed
+// pools) and must not see stray allocations, or plugins that are given a
+// device and a stream but no allocator.  For plans small enough, this entry
+// point needs nothing from the caller but the input field and the output
+// array.
 //
 // The scratch array below is part of the library's device image: every GPU on
 // which the library's module is loaded holds its kStaticScratchBytes until the

@@ -1,7 +1,7 @@
 """estimator_estimate_static: the estimate for callers that cannot allocate
-device memory (stream capture, a memory manager that owns the heap, plugins
-without an allocator) keeps its workspace in a static device array of the
-library.  Its results must equal those of estimator_estimate with a caller
+device memory (code under a memory manager that owns the device heap, plugins
+handed a device and a stream but no allocator) keeps its workspace in a
+static device array of the library.  Its results must equal those of estimator_estimate with a caller
 workspace, on repeated calls (the array keeps the previous call's contents),
 and plans too large for the array must be refused with a clear error.
 
