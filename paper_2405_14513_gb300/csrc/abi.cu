@@ -85,6 +85,9 @@ struct bisp_plan {
     // uses bytes [f region_bytes, (f + 1) region_bytes) of the workspace
     size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, region_bytes = 0;
     int last_field = 0;                  // field of the last estimate that introspection reads
+    // transform rows per block picked by the plan's autotuner (0 = default rule)
+    int rt_z = 0, rt_xy = 0;
+    int rt_gather[kMaxLevels] = {}, rt_rows[kMaxLevels] = {};
     size_t resident = 0;
     // buffers of estimator_estimate_host
     void *own_ws = nullptr, *own_in = nullptr;
@@ -312,6 +315,106 @@ int init_attributes()
     return BISP_OK;
 }
 
+// Transform tile autotuner.  Each transform kernel holds rt rows of its
+// length M in two shared-memory buffers; the best rt depends on M, the
+// kernel and the GPU (large tiles leave one block per SM).  For the forward
+// z pass, the forward row passes and each reduction grid's gather and row
+// pass, candidate tiles of 4-64 KB per buffer are timed on scratch buffers
+// holding a sample of the plan's rows (at most 64 fields of a grid, 16
+// planes, 64K z rows), and the fastest is kept.  Rows are transformed
+// independently, so the choice changes the speed, not the results.
+template <typename R>
+int autotune_transforms(bisp_plan *p, cudaStream_t s)
+{
+    using C = typename Cx<R>::T;
+    const HostPlan &P = p->hp;
+    const Rings &Rg = P.rings;
+    const int ng = P.desc.n_g, nz1 = Rg.nz + 1;
+    const int64_t ng2 = int64_t(ng) * ng;
+    Twiddles<C> tw;
+    if constexpr (sizeof(R) == 8) tw = p->tw_d; else tw = p->tw_f;
+    const int64_t zrows = std::min<int64_t>(ng2, 65536);
+    const int64_t npl = std::min<int64_t>(nz1, 16);
+    int64_t jmax = 0;
+    for (const Level &L : P.levels) jmax = std::max(jmax, std::min<int64_t>(L.njobs, 64) * L.M * L.M);
+    // scratch: z-pass input and output, the transformed planes (input of the
+    // gathers), and two buffers for the row passes
+    const size_t bz = size_t(zrows) * ng * sizeof(R);
+    const size_t bplanes = size_t(nz1) * ng2 * sizeof(C);
+    const size_t brows = std::max<size_t>(size_t(jmax), size_t(npl) * ng2) * sizeof(C);
+    const size_t bout = std::max<size_t>(size_t(nz1) * zrows * sizeof(C), brows);
+    std::vector<void *> tmp;
+    auto talloc = [&](size_t b) -> void * {
+        void *q = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(b, 256)) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        tmp.push_back(q);
+        return q;
+    };
+    auto cleanup = [&]() { for (void *q : tmp) cudaFree(q); };
+    R *zin = static_cast<R *>(talloc(bz));
+    C *planes = static_cast<C *>(talloc(bplanes));
+    C *b0 = static_cast<C *>(talloc(bout));
+    C *b1 = static_cast<C *>(talloc(brows));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!zin || !planes || !b0 || !b1 || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        if (e0) cudaEventDestroy(e0);
+        return fail(BISP_OUT_OF_MEMORY, "device memory for the transform autotuner");
+    }
+    cudaMemsetAsync(zin, 0, bz, s);
+    cudaMemsetAsync(planes, 0, bplanes, s);
+    cudaMemsetAsync(b0, 0, bout, s);
+    cudaMemsetAsync(b1, 0, brows, s);
+    const size_t cand[] = {4096, 8192, 16384, 32768, 65536};
+    // the fastest of the candidate rows per block for one launch
+    auto pick = [&](int M, int cap, auto &&launch) -> int {
+        int best = 0, last = -1;
+        float best_ms = 1e30f;
+        for (size_t bytes : cand) {
+            const int rt = std::min(int(fft_rows_per_block(M, sizeof(C), bytes)), cap);
+            if (rt == last) continue;
+            last = rt;
+            if (launch(rt) != cudaSuccess) return -1;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch(rt);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return -1;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = rt; }
+        }
+        return best;
+    };
+    const Batch one{};
+    int st = BISP_OK;
+    p->rt_z = pick(ng, 256, [&](int rt) {
+        return launch_fft_z_real<R>(zin, b0, ng, zrows, nz1, tw, one, s, rt);
+    });
+    p->rt_xy = pick(ng, ng, [&](int rt) {
+        return launch_fft_rows_T<R>(b1, b0, ng, ng, npl, nullptr, R(1), false, tw, one, s, rt);
+    });
+    if (p->rt_z < 0 || p->rt_xy < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
+    for (size_t l = 0; l < P.levels.size() && !st; ++l) {
+        const Level &L = P.levels[l];
+        const int64_t nj = std::min<int64_t>(L.njobs, 64);
+        const int g = pick(L.M, L.M, [&](int rt) {
+            return launch_ring_gather<R>(planes, ng, p->ring_arg, p->d_jobs[l], nj, L.M, false, b0, tw, one, s, rt);
+        });
+        const int r = pick(L.M, L.M, [&](int rt) {
+            return launch_fft_rows_T<R>(b0, b1, L.M, L.M, nj, nullptr, R(1), false, tw, one, s, rt);
+        });
+        if (g < 0 || r < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
+        p->rt_gather[L.lev] = std::max(g, 0);
+        p->rt_rows[L.lev] = std::max(r, 0);
+    }
+    cudaStreamSynchronize(s);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    return st;
+}
+
 int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
 {
     if (int st = init_attributes()) return st;
@@ -450,7 +553,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
     p->region_bytes = o;
     CK(cudaStreamSynchronize(s));
-    return BISP_OK;
+    return desc->precision == BISP_PREC_FP64 ? autotune_transforms<double>(p, s) : autotune_transforms<float>(p, s);
 }
 
 // Step-II launches of one estimate (one per non-empty block class)
@@ -493,17 +596,19 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     const Batch to_out{nf, fs, int64_t(P.n_bins) * P.n_lm * int64_t(sizeof(double))};
     {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
         StageMark m(p, BISP_STAGE_FORWARD, 3, s);
-        CK(launch_fft_z_real<R>(delta, A_, ng, ng2, Rg.nz + 1, tw, in_field, s));
-        CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, region, s));
-        CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, region, s));
+        CK(launch_fft_z_real<R>(delta, A_, ng, ng2, Rg.nz + 1, tw, in_field, s, p->rt_z));
+        CK(launch_fft_rows_T<R>(A_, B_, ng, ng, Rg.nz + 1, nullptr, R(1), false, tw, region, s, p->rt_xy));
+        CK(launch_fft_rows_T<R>(B_, A_, ng, ng, Rg.nz + 1, nullptr, scale, true, tw, region, s, p->rt_xy));
     }
     {   // Step I: D(r, n) on each reduction grid (Eq. iFT)
         StageMark m(p, BISP_STAGE_STEP1, int(2 * P.levels.size()), s);
         for (size_t l = 0; l < P.levels.size(); ++l) {
             const Level &L = P.levels[l];
             const int M = L.M;
-            CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, region, s));
-            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, region, s));
+            CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, region, s,
+                                     p->rt_gather[L.lev]));
+            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, region, s,
+                                    p->rt_rows[L.lev]));
         }
     }
     {   // Step II: triple sums (Eq. fftbs)

@@ -506,9 +506,9 @@ k_ntri(const double2 *__restrict__ I, const int64_t *__restrict__ ioff, const in
 
 }  // namespace
 
-size_t fft_rows_per_block(int M, size_t elem)
+size_t fft_rows_per_block(int M, size_t elem, size_t bytes)
 {
-    size_t rt = 65536 / (size_t(M) * elem);
+    size_t rt = bytes / (size_t(M) * elem);
     if (rt < 1) rt = 1;
     if (rt > 256) rt = 256;
     return rt;
@@ -516,10 +516,10 @@ size_t fft_rows_per_block(int M, size_t elem)
 
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int rt)
 {
     using C = typename Cx<R>::T;
-    const int rt = int(fft_rows_per_block(ng, sizeof(C)));
+    if (rt <= 0) rt = int(fft_rows_per_block(ng, sizeof(C)));
     const size_t smem = size_t(2) * rt * (ng + 1) * sizeof(C);
     const int64_t nblk = (rows + rt - 1) / rt;
     k_fft_z_real<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, ng, rows, nkeep, rt, tw, fb.fs_in,
@@ -530,10 +530,11 @@ cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int rt)
 {
     using C = typename Cx<R>::T;
-    const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(nrow)));
+    if (rt <= 0) rt = int(fft_rows_per_block(M, sizeof(C)));
+    rt = std::min(rt, nrow);
     const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
     const int ntile = (nrow + rt - 1) / rt;
     const int64_t nblk = nb * ntile;
@@ -546,10 +547,11 @@ cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *ou
 template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings, const Job *jobs,
                                int64_t njobs, int M, bool unit, typename Cx<R>::T *gt,
-                               const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s)
+                               const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int rt)
 {
     using C = typename Cx<R>::T;
-    const int rt = int(std::min<size_t>(fft_rows_per_block(M, sizeof(C)), size_t(M)));
+    if (rt <= 0) rt = int(fft_rows_per_block(M, sizeof(C)));
+    rt = std::min(rt, M);
     const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
     const int ntile = (M + rt - 1) / rt;
     const int64_t nblk = njobs * ntile;
@@ -674,12 +676,12 @@ cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cuda
 }
 
 // explicit instantiations
-template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const Twiddles<float2> &, const Batch &, cudaStream_t);
-template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const Twiddles<double2> &, const Batch &, cudaStream_t);
-template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const Twiddles<float2> &, const Batch &, cudaStream_t);
-template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t);
-template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t);
-template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t);
+template cudaError_t launch_fft_z_real<float>(const float *, float2 *, int, int64_t, int, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_fft_z_real<double>(const double *, double2 *, int, int64_t, int, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int, int64_t, const int64_t *, float, bool, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, int, cudaStream_t);
 template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, int, cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);

@@ -67,7 +67,7 @@ struct StepIIArgs {
 // frequencies [0, nkeep) written transposed as out[k][row].
 template <typename R>
 cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64_t rows, int nkeep,
-                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int rt = 0);
 
 // Batched row transforms written transposed: in[b][nrow][M] -> out[b][M][nrow]
 // (out at out_off[b] when out_off is not null, else b * M * nrow), times
@@ -75,7 +75,8 @@ cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64
 template <typename R>
 cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int nrow,
                               int64_t nb, const int64_t *out_off, R scale, bool zero_dc,
-                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s);
+                              const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s,
+                              int rt = 0);
 
 // Step I, first pass: ring r of plane n of Delta (planes [nz+1][ng][ng]),
 // folded onto the M x M grid, transformed along u_y, written transposed to
@@ -84,7 +85,7 @@ template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings,
                                const Job *jobs, int64_t njobs, int M, bool unit,
                                typename Cx<R>::T *gt, const Twiddles<typename Cx<R>::T> &tw,
-                               const Batch &fb, cudaStream_t s);
+                               const Batch &fb, cudaStream_t s, int rt = 0);
 
 // Step II: partial triple sums of every unit, one block per unit, one launch
 // per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
@@ -138,6 +139,10 @@ cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32
                         int64_t ntriples, const GridArg &grids, double *raw, cudaStream_t s);
 
 // Sizes of dynamic shared memory (bytes) of the transform kernels.
-size_t fft_rows_per_block(int M, size_t elem);
+// Rows of length M a transform block holds: each of its two shared-memory
+// buffers takes about `bytes` (1 .. 256 rows).  rt = 0 passed to the
+// launchers above selects this with the default 16 KB; the plan's autotuner
+// passes its own choice.
+size_t fft_rows_per_block(int M, size_t elem, size_t bytes = 16384);
 
 }  // namespace bisp

@@ -341,3 +341,18 @@ def test_grid_384_sampled_sums():
     want = O.combo_sums(field.astype(np.float64), L, tab["ints"][np.array(pick)]).real
     assert np.abs(S[np.array(pick)] - want).max() < TOL["mixed_tc"] * np.sqrt(np.mean(want ** 2))
     plan.close()
+
+
+def test_transform_tiles_do_not_change_results():
+    """The plan's autotuner picks transform tiles by timing; rows are
+    transformed independently, so two plans of one configuration (tuned
+    separately) must give bit-identical estimates."""
+    ng, L = 64, 1000.0
+    edges = synth.default_k1_edges(ng, L, 6)
+    f = torch.from_numpy(synth.make_field(ng, L, 41).astype(np.float32)).cuda()[None].contiguous()
+    outs = []
+    for _ in range(2):
+        plan = api.Plan(ng, L, edges, 5, 5, 6, precision="mixed_tc")
+        outs.append(plan.estimate(f, plan.workspace(1)).cpu().numpy())
+        plan.close()
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
