@@ -631,7 +631,8 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     {   // binning and the ratio of Eq. bs_lm2_1
         StageMark m(p, BISP_STAGE_BIN, 1, s);
         CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
-                              1.0 / (P.volume * double(ng2)), B, to_out, s));
+                              1.0 / (P.volume * double(ng2)), B, to_out, s,
+                              p->precision != BISP_PREC_FP64));
     }
     p->last_field = batch - 1;
     return BISP_OK;

@@ -407,7 +407,10 @@ __constant__ double c_pref[9];
 // Legendre recurrence ratios (2l+1)/(l+1-m) and (l+m)/(l+1-m), l, m <= 8
 __constant__ double c_rec[2][9][9];
 
-template <typename W, int LMAX>
+// W: type of the sums over records; Y: type the Y_lm of each record are
+// computed in (FP32 for the FP32-transform paths, whose tolerance is 1e-4;
+// FP64 for the FP64 path and the plan-time denominators).
+template <typename W, typename Y, int LMAX>
 __global__ void __launch_bounds__(256)
 k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ bin_start, int64_t nbins,
            const double *__restrict__ value, const double *__restrict__ den, double norm,
@@ -425,35 +428,35 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
     const int64_t k0 = bin_start[b], k1 = bin_start[b + 1];
     for (int64_t k = k0 + lane; k < k1; k += 32) {
         const Record R = rec[k];
-        const W x = W(R.pz), c = W(R.cphi);
+        const Y x = Y(R.pz), c = Y(R.cphi);
         const W mult = (R.flags & 1) ? W(1) : W(2);
         const W v = W(mode == 0 ? value[R.s_index] : value[k]) * mult;
         const bool deg = (R.flags & 2) != 0;
-        const W s = sqrt(max(W(0), W(1) - x * x));
-        W pmm = W(1), tm1 = W(1), tm2 = W(1);   // P_m^m; cos(m phi), cos((m-1) phi)
+        const Y s = sqrt(max(Y(0), Y(1) - x * x));
+        Y pmm = Y(1), tm1 = Y(1), tm2 = Y(1);   // P_m^m; cos(m phi), cos((m-1) phi)
 #pragma unroll
         for (int m = 0; m <= LMAX; ++m) {
-            W tm;
-            if (m == 0) tm = W(1);
+            Y tm;
+            if (m == 0) tm = Y(1);
             else if (m == 1) tm = c;
-            else tm = W(2) * c * tm1 - tm2;
-            if (m > 0) pmm *= -W(2 * m - 1) * s;
-            W plm1 = W(0), pl = pmm;                 // P_{l-1}^m, P_l^m at l = m
+            else tm = Y(2) * c * tm1 - tm2;
+            if (m > 0) pmm *= -Y(2 * m - 1) * s;
+            Y plm1 = Y(0), pl = pmm;                 // P_{l-1}^m, P_l^m at l = m
 #pragma unroll
             for (int l = m; l <= LMAX; ++l) {
                 if ((l & 1) == 0) {
-                    const W y = W(c_nlm[l][m]) * pl;
+                    const Y y = Y(c_nlm[l][m]) * pl;
                     const int idx = (l >> 1) * (l >> 1) + m;
                     if (mode == 0) {
-                        const W w = deg ? (m == 0 ? y : W(0)) : y * tm;
-                        acc[idx] += w * v;
+                        const Y w = deg ? (m == 0 ? y : Y(0)) : y * tm;
+                        acc[idx] += W(w) * v;
                     } else {
-                        acc[idx] += y * y * v;
+                        acc[idx] += W(y) * W(y) * v;
                     }
                 }
                 // P_{l+1}^m = ((2l+1) x P_l^m - (l+m) P_{l-1}^m) / (l+1-m), with
                 // the two ratios from constant memory (no division per record)
-                const W pn = W(c_rec[0][l][m]) * x * pl - W(c_rec[1][l][m]) * plm1;
+                const Y pn = Y(c_rec[0][l][m]) * x * pl - Y(c_rec[1][l][m]) * plm1;
                 plm1 = pl;
                 pl = pn;
             }
@@ -607,23 +610,32 @@ cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const d
     return cudaGetLastError();
 }
 
-template <typename W>
-cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
-                            const double *value, int l_max, const double *den, double norm, double *out,
-                            const Batch &fb, cudaStream_t s)
+template <typename W, typename Y>
+cudaError_t epilogue_lmax(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins, const double *value,
+                          int l_max, const double *den, double norm, double *out, const Batch &fb, cudaStream_t s)
 {
-    if (nbins == 0) return cudaSuccess;
     const dim3 grid(unsigned((nbins * 32 + 255) / 256), fb.nf);
     const int64_t fi = fb.fs_in, fo = fb.fs_out;
     switch (l_max) {
-    case 0: k_epilogue<W, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 2: k_epilogue<W, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 4: k_epilogue<W, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 6: k_epilogue<W, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 8: k_epilogue<W, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 0: k_epilogue<W, Y, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 2: k_epilogue<W, Y, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 4: k_epilogue<W, Y, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 6: k_epilogue<W, Y, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    case 8: k_epilogue<W, Y, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <typename W>
+cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
+                            const double *value, int l_max, const double *den, double norm, double *out,
+                            const Batch &fb, cudaStream_t s, bool fp32_weights)
+{
+    if (nbins == 0) return cudaSuccess;
+    if (fp32_weights)
+        return epilogue_lmax<W, float>(mode, rec, bin_start, nbins, value, l_max, den, norm, out, fb, s);
+    return epilogue_lmax<W, W>(mode, rec, bin_start, nbins, value, l_max, den, norm, out, fb, s);
 }
 
 // Every kernel that takes more than 48 KB of dynamic shared memory is
@@ -686,7 +698,7 @@ template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, con
 template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, int, cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
 template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
-template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t);
-template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t);
+template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t, bool);
+template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t, bool);
 
 }  // namespace bisp

@@ -125,10 +125,11 @@ cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const d
 
 // Binning epilogue of Eq. bs_lm2_1.  mode 0: B = sqrt((2l+1)/4pi) num /
 // (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
+// fp32_weights: the Y_lm of each record in FP32 (sums stay in W).
 template <typename W>
 cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
                             const double *value, int l_max, const double *den, double norm,
-                            double *out, const Batch &fb, cudaStream_t s);
+                            double *out, const Batch &fb, cudaStream_t s, bool fp32_weights = false);
 
 // Y_lm normalisations nlm[l][m] and the prefactors sqrt((2l+1)/(4 pi)).
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);
