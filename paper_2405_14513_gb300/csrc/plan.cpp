@@ -212,6 +212,25 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
         if (cur_flags & 1) return "tcgen05 tiles need n1 >= 0";
         if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows || tc_stages(T.ncol, T.nslot) == 0)
             return "tcgen05 tile limits";
+        // rows (tensor-memory lanes) in order of their D1 field, then D2
+        // field, and the staged fields numbered in that order: lanes of one
+        // shared-memory load phase then read the same D1 row (a broadcast) or
+        // consecutive slots (different banks)
+        auto keys = [&](const std::pair<int32_t, int32_t> &gr) {
+            const Group &G = P.groups[gr.first];
+            const Row &rw = P.rows[gr.second];
+            const int a1 = G.n1 < 0 ? -G.n1 : G.n1, a2 = G.n2 < 0 ? -G.n2 : G.n2;
+            return std::make_pair((a1 << 8) | rw.r1, (a2 << 8) | rw.r2);
+        };
+        std::stable_sort(cur.rows.begin(), cur.rows.end(),
+                         [&](const auto &x, const auto &y) { return keys(x) < keys(y); });
+        cur.slots.clear();
+        for (auto &gr : cur.rows) {
+            const auto k = keys(gr);
+            if (slot_of(cur.slots, k.first) < 0) cur.slots.push_back(k.first);
+            if (slot_of(cur.slots, k.second) < 0) cur.slots.push_back(k.second);
+        }
+        if (int(cur.slots.size()) != T.nslot) return "tcgen05 tile slots";
         for (auto &gr : cur.rows) {
             const Group &G = P.groups[gr.first];
             const Row &rw = P.rows[gr.second];
