@@ -729,7 +729,14 @@ static void sums_direct(const rings_t *R, const cplx *cube, const combo_t *c, lo
 /*   (numerator already divided by V N_g^2).  Returns the number of accepted */
 /*   combinations, or -1.                                                    */
 /* ------------------------------------------------------------------------ */
-long bo_estimate(const bo_desc *d, const double *delta, double *B, double *num_re, double *num_im, double *den)
+/* Share `part` of `nparts` (bo_estimate_part): the numerator sums only the
+ * combinations whose ordered plane pair (n1, n2) has index
+ * (n1 + nz)(2 nz + 1) + (n2 + nz) congruent to `part` modulo `nparts`; the
+ * denominator sums all of them.  The numerator being a plain sum over
+ * combinations, the shares' B add up to the whole B.  (nparts = 1: every
+ * combination.) */
+static long estimate_share(const bo_desc *d, const double *delta, int part, int nparts, double *B, double *num_re,
+                           double *num_im, double *den)
 {
     if (desc_check(d)) return -1;
     set_threads(d->nthreads);
@@ -754,10 +761,12 @@ long bo_estimate(const bo_desc *d, const double *delta, double *B, double *num_r
     double norm = 1.0 / (V * (double)d->ng * (double)d->ng);
     for (long k = 0; k < nc; ++k) {
         const geom_t *g = &c[k].g;
+        const long pair = (long)(c[k].n1 + R.nz) * (2 * R.nz + 1) + (c[k].n2 + R.nz);
+        const int mine = pair % nparts == part;
         for (int l = 0; l <= d->l_max; ++l)
             for (int m = 0; m <= l; ++m) {
                 long o = (long)g->bin * nlm + lm_index(l, m);
-                num[o] += combo_ystar(l, m, g) * S[k] * norm;
+                if (mine) num[o] += combo_ystar(l, m, g) * S[k] * norm;
                 dn[o] += (double)c[k].ntri * combo_y2(l, m, g);
             }
     }
@@ -778,6 +787,17 @@ long bo_estimate(const bo_desc *d, const double *delta, double *B, double *num_r
     free(ntri);
     free(R.ringidx);
     return nc;
+}
+
+long bo_estimate(const bo_desc *d, const double *delta, double *B, double *num_re, double *num_im, double *den)
+{
+    return estimate_share(d, delta, 0, 1, B, num_re, num_im, den);
+}
+
+long bo_estimate_part(const bo_desc *d, const double *delta, int part, int nparts, double *B)
+{
+    if (nparts < 1 || part < 0 || part >= nparts) return -1;
+    return estimate_share(d, delta, part, nparts, B, NULL, NULL, NULL);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -62,6 +62,8 @@ def _load():
             lib.bo_ylm.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, dp]
             lib.bo_estimate.argtypes = [C.POINTER(Desc), dp, dp, dp, dp, dp]
             lib.bo_estimate.restype = C.c_long
+            lib.bo_estimate_part.argtypes = [C.POINTER(Desc), dp, C.c_int, C.c_int, dp]
+            lib.bo_estimate_part.restype = C.c_long
             lib.bo_combos.argtypes = [C.POINTER(Desc), C.c_int, C.c_long, ip, lp, ip, dp]
             lib.bo_combos.restype = C.c_long
             lib.bo_combo_sums.argtypes = [C.c_int, C.c_double, dp, C.c_long, ip, C.c_int, dp, dp]
@@ -189,6 +191,20 @@ def estimate(delta, box_len, k1_edges, n_mu, n_t, l_max, direct=False, nthreads=
     if nc < 0:
         raise ValueError("invalid estimator parameters")
     return {"B": B, "num_re": nr_, "num_im": ni_, "den": dn_, "n_combos": int(nc)}
+
+
+def estimate_part(delta, box_len, k1_edges, n_mu, n_t, l_max, part, nparts, direct=False, nthreads=0):
+    """Share `part` of `nparts` of estimate(...)["B"]: the numerator over the
+    combinations whose ordered plane pair (n1, n2) has index
+    (n1 + nz)(2 nz + 1) + (n2 + nz) = part (mod nparts), divided by the whole
+    denominator.  The shares sum to the whole B."""
+    d_arr = np.ascontiguousarray(delta, dtype=np.float64)
+    ng = d_arr.shape[0]
+    desc, keep = _desc(ng, box_len, k1_edges, n_mu, n_t, l_max, direct, nthreads)
+    B = np.zeros((len(keep) - 1, n_mu, n_t, n_moments_all(l_max)))
+    if _load().bo_estimate_part(C.byref(desc), _dp(d_arr), int(part), int(nparts), _dp(B)) < 0:
+        raise ValueError("invalid estimator parameters")
+    return B
 
 
 def select_even(arr: np.ndarray, l_max: int) -> np.ndarray:
