@@ -154,8 +154,15 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-# source file of the Step-II kernel of each precision mode
-STEP2_SOURCE = {"mixed_tc": "step2_tc.cu", "mixed": "kernels.cu", "fp32": "kernels.cu", "fp64": "kernels.cu"}
+# source that decides the Step-II kernel's DRAM traffic, per precision mode:
+# (file, first line, end marker) regions; None = the file's start / end
+STEP2_SOURCE = {
+    "mixed_tc": [("step2_tc.cu", None, "template <int NC>\ncudaError_t launch_class"),
+                 ("plan.hpp", "constexpr int kTcRows", "struct TcUnit"),
+                 ("plan.cpp", "std::string build_tc(", "}  // namespace\n\nstd::string enumerate(")],
+    "mixed": [("kernels.cu", None, None)], "fp32": [("kernels.cu", None, None)],
+    "fp64": [("kernels.cu", None, None)],
+}
 
 
 def _traffic(ng, precision):
@@ -173,10 +180,36 @@ def _traffic(ng, precision):
 
 
 def _kernel_digest(precision):
+    """Digest of the Step-II kernel source regions of a precision mode (the
+    kernel and the tiling that decides what it reads)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2405_14513_gb300", "csrc", STEP2_SOURCE[precision])
-    with open(src, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name, start, end in STEP2_SOURCE[precision]:
+        with open(os.path.join(ROOT, "paper_2405_14513_gb300", "csrc", name)) as fh:
+            text = fh.read()
+        a = text.index(start) if start else 0
+        b = text.index(end, a) if end else len(text)
+        h.update(text[a:b].encode())
+    return h.hexdigest()[:16]
+
+
+def fft_crosscheck(plan, field, ws, box):
+    """Our forward transform against cuFFT: largest |ours - ref| / max |ref|
+    over planes 0, 1 and N_g/3 of Delta = (V/N^3) DFT(delta), Delta(0) = 0,
+    ours the FP32 planes the last estimate left in the workspace, ref
+    torch.fft.fftn (cuFFT) in FP64.  Not timed."""
+    import torch
+    ng = plan.n_g
+    ref = torch.fft.fftn(field.double()) * (box ** 3 / ng ** 3)
+    ref[0, 0, 0] = 0
+    err = 0.0
+    for n in (0, 1, ng // 3):
+        got = plan.delta_plane(ws, n)
+        want = ref[:, :, n].cpu().numpy()
+        err = max(err, float(np.abs(got - want).max() / np.abs(want).max()))
+    del ref
+    torch.cuda.empty_cache()
+    return {"ref": "cuFFT via torch.fft.fftn, FP64", "planes": [0, 1, ng // 3], "max_rel_err": err}
 
 
 def _peaks():
@@ -274,18 +307,21 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2405_14513_gb300 import api, synth
+    from paper_2405_14513_gb300 import api, shard, synth
 
     rank, world, local = _dist()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
+    shares = args.split == "shares" and world > 1
     W = WORKLOADS[args.workload]
     ng = W["ng"]
     cfg, edges = workload(W, args.precision)
+    cfg["split"] = "shares" if shares else "replicas"
     plan = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=1)
-    field = synth.make_field_torch(ng, W["box"], 1 + rank, device=dev).to(torch.float32).contiguous()
+    # replicas: one field per rank; shares: every rank holds the same field
+    field = synth.make_field_torch(ng, W["box"], 1 if shares else 1 + rank, device=dev).to(torch.float32).contiguous()
     ws = plan.workspace(1, device=dev)
     out = torch.empty(plan.out_shape(1), dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -294,8 +330,14 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    def step():
+        if shares:
+            shard.estimate_sharded(plan, field, ws, out=out)
+        else:
+            plan.estimate(field, ws, out=out, stream=stream)
+
     for _ in range(args.warmup):
-        plan.estimate(field, ws, out=out, stream=stream)
+        step()
     torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
@@ -305,7 +347,7 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        plan.estimate(field, ws, out=out, stream=stream)
+        step()
     t1.record(stream)
     torch.cuda.synchronize(dev)
     barrier()
@@ -316,21 +358,34 @@ def run_ours(args):
     plan.set_timing(False)
     flops = plan.stage_flops()
     ms = max_over_ranks(ms, device=dev)
-    value = job_rate(plan.n_bins, world, ms / 1e3)
+    fields_per_step = 1 if shares else world
+    value = job_rate(plan.n_bins, fields_per_step, ms / 1e3)
     finite = bool(torch.isfinite(out).any().item())
+    fft_check = fft_crosscheck(plan, field, ws, W["box"])
 
-    # end to end through the host entry point: pinned field in, B out, copies timed
+    # end to end through the host side: pinned field in, B out, copies timed
     host = field.cpu().pin_memory()
     host_np = host.numpy()
-    out_h = torch.empty(plan.out_shape(1), dtype=torch.float64).pin_memory().numpy()
-    plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
+    out_pin = torch.empty(plan.out_shape(1), dtype=torch.float64).pin_memory()
+    out_h = out_pin.numpy()
+
+    def step_host():
+        if shares:
+            field.copy_(host, non_blocking=True)
+            shard.estimate_sharded(plan, field, ws, out=out)
+            out_pin.copy_(out, non_blocking=True)
+            stream.synchronize()
+        else:
+            plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
+
+    step_host()
     barrier()
     te = time.perf_counter()
     for _ in range(args.steps):
-        plan.estimate_host(host_np, out=out_h, stream=stream.cuda_stream)
+        step_host()
     te = (time.perf_counter() - te) / args.steps
     te = max_over_ranks(te, device=dev)
-    e2e = {"value": job_rate(plan.n_bins, world, te), "unit": "configs/s",
+    e2e = {"value": job_rate(plan.n_bins, fields_per_step, te), "unit": "configs/s",
            "h2d_bytes_per_step": int(host.numel() * host.element_size()),
            "d2h_bytes_per_step": int(out_h.size * 8)}
 
@@ -354,13 +409,24 @@ def run_ours(args):
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                  "traffic": _traffic(ng, args.precision), "flops_per_estimate": flops["step2"],
                  "ms_per_estimate": s2_ms, "launches_per_estimate": st_n["step2"] / args.steps})
+    # Step I (HBM-bound transforms): algorithmic bytes = the D store written
+    # once + the kept planes of Delta read once, over its own event time
+    bf16_, hbm, src_ = _peaks()
+    s1_ms = st_ms["step1"] / args.steps
+    s1_bytes = plan.info["dstore_bytes"] + (ng // 3 + 1) * ng * ng * (16 if args.precision == "fp64" else 8)
+    roof1 = {"kernels": "k_ring_gather + k_fft_rows_T (Step I, per reduction grid)", "bound": "hbm",
+             "achieved": s1_bytes / (s1_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+             "frac": s1_bytes / (s1_ms / 1e3) / 1e9 / hbm, "bytes_per_estimate": s1_bytes,
+             "ms_per_estimate": s1_ms, "peak_source": f"{src_} HBM copy bandwidth"}
     stage_share = {k: st_ms[k] / max(sum(st_ms.values()), 1e-9) for k in st_ms}
     launches = int(sum(st_n.values()))
 
     line = {"metric": METRIC.format(ng=ng), "value": value, "unit": "configs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if shares else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-            "e2e": e2e, "roofline": roof, "gpu_launches": launches, "clocks": clk,
+            "e2e": e2e, "roofline": roof, "roofline_step1": roof1, "fft_crosscheck": fft_check,
+            "gpu_launches": launches, "clocks": clk,
             "stage_ms_per_step": {k: v / args.steps for k, v in st_ms.items()},
             "stage_share": stage_share, "output_finite": finite,
             "plan": {k: plan.info[k] for k in ("n_combos", "n_pairs", "n_items", "n_levels",
@@ -521,6 +587,9 @@ def main(argv=None):
                     help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, "
                          "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", default="replicas", choices=["replicas", "shares"],
+                    help="N > 1: replicas (a field per rank, weak scaling; the default) or shares (one "
+                         "field's Step II split over the ranks, one all-reduce; strong scaling)")
     ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
                     help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
     args = ap.parse_args(argv)

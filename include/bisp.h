@@ -77,6 +77,12 @@ typedef struct {
     int l_max;                /* even, 0..8                                        */
     int precision;            /* bisp_precision                                    */
     int max_batch;            /* largest batch passed to estimator_estimate, 1..65535 */
+    const int *n_mu_l;        /* optional HOST pointers, both or neither (NULL): l_max/2 + 1 */
+    const int *n_t_l;         /* entries, the (mu, t) bins of the moments of order l = 0, 2, */
+                              /* .., l_max (each in [1, 4096]); n_mu and n_t are then      */
+                              /* ignored.  Not kept after estimator_plan returns.  The      */
+                              /* paper bins l = 0, 2 finer than l = 4, 6 (Sec. III.B,        */
+                              /* appendix); see bisp_view_info for the output layout.       */
 } bisp_desc;
 
 typedef struct {
@@ -91,7 +97,23 @@ typedef struct {
     size_t dstore_bytes;             /* D-field store of one field                    */
     size_t workspace_bytes;          /* estimator_workspace_bytes(plan, 1)            */
     size_t resident_bytes;           /* device memory owned by the plan               */
+    int n_views;                     /* binnings (bisp_view_info), >= 1                */
+    int64_t out_doubles;             /* doubles of B per field (all views)            */
 } bisp_plan_info;
+
+/* A binning of the output.  Consecutive even l with the same (mu, t) grid
+ * share a view; without per-l grids there is one view, l = 0 .. l_max on
+ * n_mu x n_t, and B of a field is exactly [n_k1][n_mu][n_t][n_lm].  In
+ * general B of a field is the views' blocks one after another, block v
+ * [n_k1][n_mu][n_t][n_lm] (its own n_mu, n_t, n_lm) at `offset` doubles;
+ * moments in the order (l, m) = (l_lo, 0) .. (l_hi, l_hi), even l. */
+typedef struct {
+    int l_lo, l_hi;                  /* even orders of the view's moments            */
+    int n_mu, n_t;                   /* its (mu, t) grid                             */
+    int n_lm;                        /* moments: (l_hi/2 + 1)^2 - (l_lo/2)^2          */
+    int64_t n_bins;                  /* n_k1 n_mu n_t                                 */
+    int64_t offset;                  /* first double of the block in a field's B      */
+} bisp_view_info;
 
 /* Build a plan (Sec. II: ring table, N_tri by Eq. Ntri2 on the GPU in FP64,
  * combination table with its (k1, mu, t) bins and the field-independent
@@ -102,6 +124,10 @@ int estimator_plan(bisp_plan **out, const bisp_desc *desc, void *stream);
 
 /* Plan summary.  info: host pointer. */
 int estimator_plan_info(const bisp_plan *plan, bisp_plan_info *info);
+
+/* Binning `view` (0 <= view < n_views) of the plan's output.  info: host
+ * pointer.  BISP_INVALID_ARG for a view out of range. */
+int estimator_view_info(const bisp_plan *plan, int view, bisp_view_info *info);
 
 /* Bytes of device workspace estimator_estimate needs for `batch` fields
  * (0 on a bad argument): batch regions of one field's size.  All fields of
@@ -115,7 +141,9 @@ size_t estimator_workspace_bytes(const bisp_plan *plan, int batch);
  *   workspace: DEVICE pointer to >= estimator_workspace_bytes(plan, batch)
  *              bytes, 256-byte aligned, owned by the caller; contents are
  *              scratch between calls;
- *   B:         DEVICE pointer, [batch][n_k1][n_mu][n_t][n_lm] double.
+ *   B:         DEVICE pointer, [batch][out_doubles] double: per field the
+ *              views' blocks (bisp_view_info); with one view
+ *              [batch][n_k1][n_mu][n_t][n_lm].
  * Asynchronous: all work is ordered on `stream`.  Calls that share a plan
  * or a workspace must not overlap on the device. */
 int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *workspace,
@@ -126,6 +154,37 @@ int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *work
  * its own device workspace and staging buffers for max_batch fields. */
 int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
                             void *stream);
+
+/* One share of an estimate, for splitting one field over several devices
+ * (each holding its own plan).  The numerator of Eq. bs_lm2_1 is a sum over
+ * combinations of Re Y_lm S (S of Eq. fftbs), so it splits over any
+ * partition of the combinations; this call runs the transforms and Step I
+ * whole and the Step-II triple sums of share `part` of `nparts` (the
+ * Step-II blocks of each kind split into nparts contiguous runs of about
+ * equal cost), and writes
+ *   B_part = sqrt((2l+1)/4pi) num_part / (V N_g^2 den),
+ * num_part the numerator over the share's combinations, den the whole
+ * denominator (plan-resident), NaN where den = 0.  The element-wise sum of
+ * B_part over part = 0 .. nparts - 1 is B of estimator_estimate up to FP64
+ * rounding (NaN bins stay NaN): one sum-reduction of the output between
+ * devices completes the estimate.  Arguments as for estimator_estimate;
+ * 0 <= part < nparts, else BISP_INVALID_ARG.  nparts = 1 is the whole
+ * estimate.  (The paper has no counterpart: it runs on one CPU node.) */
+int estimator_estimate_part(bisp_plan *plan, const void *delta, int batch, void *workspace, double *B_part,
+                            int part, int nparts, void *stream);
+
+/* Running statistics of B over many fields (mocks): the spread of the
+ * estimates over realisations is what the paper compares deviations with
+ * (Sec. III.B).  For i < n, the values B[f][i], f = 0 .. batch - 1, join
+ * count[i], mean[i] and m2[i] (sum of squared deviations from the mean) by
+ * Welford's update in FP64, in field order; non-finite values (empty bins)
+ * are skipped.  The sample variance is m2 / (count - 1).  All DEVICE
+ * pointers: B [batch][n] (n = out_doubles for whole outputs), count, mean,
+ * m2 [n], zero before the first update, owned by the caller.
+ * Stream-ordered.  (The paper has no counterpart: it reports its 50
+ * realisations' spread without saying how it was accumulated.) */
+int estimator_stats_update(const double *B, int batch, int64_t n, int64_t *count, double *mean, double *m2,
+                           void *stream);
 
 /* ---------------- captured estimates (CUDA graphs) ---------------- */
 
@@ -223,7 +282,8 @@ int estimator_stage_flops(const bisp_plan *plan, double *flops);
 /* ---------------- introspection, for tests and diagnostics ---------------- */
 
 /* Denominators sum_c |Y_lm(p_c)|^2 N_tri,c of Eq. bs_lm2_1 (counted over both
- * members of each +-n pair).  den: HOST pointer [n_bins][n_lm]. */
+ * members of each +-n pair).  den: HOST pointer [out_doubles], laid out as
+ * a field's B. */
 int estimator_denominator(const bisp_plan *plan, double *den);
 
 /* Accepted combinations, one of each pair (n1, n2) / (-n1, -n2), kept with

@@ -31,7 +31,8 @@ class BispError(RuntimeError):
 class Desc(C.Structure):
     _fields_ = [("n_g", C.c_int), ("box_len", C.c_double), ("n_k1", C.c_int),
                 ("k1_edges", C.POINTER(C.c_double)), ("n_mu", C.c_int), ("n_t", C.c_int),
-                ("l_max", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int)]
+                ("l_max", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int),
+                ("n_mu_l", C.POINTER(C.c_int)), ("n_t_l", C.POINTER(C.c_int))]
 
 
 class PlanInfo(C.Structure):
@@ -40,7 +41,12 @@ class PlanInfo(C.Structure):
                 ("n_levels", C.c_int), ("n_bins", C.c_int64), ("n_combos", C.c_int64),
                 ("n_pairs", C.c_int64), ("n_items", C.c_int64), ("triple_products", C.c_double),
                 ("dstore_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t),
-                ("resident_bytes", C.c_size_t)]
+                ("resident_bytes", C.c_size_t), ("n_views", C.c_int), ("out_doubles", C.c_int64)]
+
+
+class ViewInfo(C.Structure):
+    _fields_ = [("l_lo", C.c_int), ("l_hi", C.c_int), ("n_mu", C.c_int), ("n_t", C.c_int), ("n_lm", C.c_int),
+                ("n_bins", C.c_int64), ("offset", C.c_int64)]
 
 
 def load():
@@ -55,12 +61,18 @@ def load():
         lib.estimator_plan.restype = C.c_int
         lib.estimator_plan_info.argtypes = [vp, C.POINTER(PlanInfo)]
         lib.estimator_plan_info.restype = C.c_int
+        lib.estimator_view_info.argtypes = [vp, C.c_int, C.POINTER(ViewInfo)]
+        lib.estimator_view_info.restype = C.c_int
         lib.estimator_workspace_bytes.argtypes = [vp, C.c_int]
         lib.estimator_workspace_bytes.restype = C.c_size_t
         lib.estimator_estimate.argtypes = [vp, vp, C.c_int, vp, vp, vp]
         lib.estimator_estimate.restype = C.c_int
         lib.estimator_estimate_host.argtypes = [vp, vp, C.c_int, vp, vp]
         lib.estimator_estimate_host.restype = C.c_int
+        lib.estimator_estimate_part.argtypes = [vp, vp, C.c_int, vp, vp, C.c_int, C.c_int, vp]
+        lib.estimator_estimate_part.restype = C.c_int
+        lib.estimator_stats_update.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp]
+        lib.estimator_stats_update.restype = C.c_int
         lib.estimator_destroy.argtypes = [vp]
         lib.estimator_destroy.restype = None
         lib.estimator_status_string.argtypes = [C.c_int]
@@ -143,7 +155,10 @@ class Plan:
     """An estimator plan (``estimator_plan``) and its calls."""
 
     def __init__(self, n_g: int, box_len: float, k1_edges, n_mu: int, n_t: int, l_max: int,
-                 precision: str = "mixed", max_batch: int = 1, stream=None):
+                 precision: str = "mixed", max_batch: int = 1, stream=None, mu_t_bins_l=None):
+        """mu_t_bins_l: optional per-l (mu, t) grids, one entry per even l <= l_max,
+        each n (an n x n grid) or (n_mu, n_t); n_mu and n_t are then ignored and
+        the output is laid out by view (``views``, ``split``)."""
         lib = load()
         self._edges = np.ascontiguousarray(k1_edges, dtype=np.float64)
         self.n_g, self.box_len, self.n_mu, self.n_t, self.l_max = n_g, box_len, n_mu, n_t, l_max
@@ -152,6 +167,14 @@ class Plan:
         self.max_batch = max_batch
         d = Desc(n_g, box_len, self.n_k1, _dp(self._edges), n_mu, n_t, l_max,
                  PRECISIONS[precision], max_batch)
+        if mu_t_bins_l is not None:
+            g = [(int(x), int(x)) if np.isscalar(x) else (int(x[0]), int(x[1])) for x in mu_t_bins_l]
+            if len(g) != l_max // 2 + 1:
+                raise ValueError("mu_t_bins_l needs one entry per even l <= l_max")
+            mu_l = (C.c_int * len(g))(*[a for a, _ in g])
+            t_l = (C.c_int * len(g))(*[b for _, b in g])
+            d.n_mu_l = C.cast(mu_l, C.POINTER(C.c_int))
+            d.n_t_l = C.cast(t_l, C.POINTER(C.c_int))
         h = C.c_void_p()
         st = lib.estimator_plan(C.byref(h), C.byref(d), _stream_handle(stream) if stream is not None
                                 else C.c_void_p(0))
@@ -163,6 +186,13 @@ class Plan:
         self.n_lm = inf.n_lm
         self.n_bins = inf.n_bins
         self.n_combos = inf.n_combos
+        self.n_mu, self.n_t = inf.n_mu, inf.n_t
+        self.out_doubles = inf.out_doubles
+        self.views = []
+        for v in range(inf.n_views):
+            vi = ViewInfo()
+            _check(lib.estimator_view_info(h, v, C.byref(vi)), "estimator_view_info")
+            self.views.append({k: getattr(vi, k) for k, _ in ViewInfo._fields_})
         self.field_dtype = np.float64 if precision == "fp64" else np.float32
 
     # ------------------------------------------------------------------
@@ -178,7 +208,18 @@ class Plan:
             pass
 
     def out_shape(self, batch: int = 1):
-        return (batch, self.n_k1, self.n_mu, self.n_t, self.n_lm)
+        """[batch][n_k1][n_mu][n_t][n_lm] with one view, else [batch][out_doubles]."""
+        if len(self.views) == 1:
+            return (batch, self.n_k1, self.n_mu, self.n_t, self.n_lm)
+        return (batch, self.out_doubles)
+
+    def split(self, out):
+        """The views' blocks of an output (torch tensor or numpy array, first
+        axis the batch): a list of [batch][n_k1][n_mu][n_t][n_lm] arrays, one
+        per view, moments of orders view["l_lo"] .. view["l_hi"]."""
+        flat = out.reshape(out.shape[0], self.out_doubles)
+        return [flat[:, v["offset"]:v["offset"] + v["n_bins"] * v["n_lm"]].reshape(
+                    out.shape[0], self.n_k1, v["n_mu"], v["n_t"], v["n_lm"]) for v in self.views]
 
     def workspace_bytes(self, batch: int = 1) -> int:
         return int(load().estimator_workspace_bytes(self._h, batch))
@@ -211,6 +252,22 @@ class Plan:
         _check(st, "estimator_estimate")
         return out
 
+    def estimate_part(self, delta, workspace, part: int, nparts: int, out=None, stream=None):
+        """Share `part` of `nparts` of estimate(delta) (``estimator_estimate_part``):
+        the shares' outputs sum to the whole estimate."""
+        import torch
+        if delta.dim() == 3:
+            delta = delta.unsqueeze(0)
+        batch = delta.shape[0]
+        self._check_field(delta)
+        if out is None:
+            out = torch.empty(self.out_shape(batch), dtype=torch.float64, device=delta.device)
+        st = load().estimator_estimate_part(self._h, C.c_void_p(delta.data_ptr()), batch,
+                                            C.c_void_p(workspace.data_ptr()), C.c_void_p(out.data_ptr()),
+                                            int(part), int(nparts), _stream_handle(stream))
+        _check(st, "estimator_estimate_part")
+        return out
+
     def graph(self, delta, workspace, out, stream=None) -> "Graph":
         """Capture estimate(delta, workspace, out) into a CUDA graph
         (``estimator_graph_create``); the tensors must outlive the graph."""
@@ -237,9 +294,10 @@ class Plan:
 
     # ------------------------------------------------------------------
     def denominator(self) -> np.ndarray:
-        den = np.zeros((self.n_bins, self.n_lm))
+        """Denominators laid out as one field's output (out_shape(1)[1:])."""
+        den = np.zeros(self.out_doubles)
         _check(load().estimator_denominator(self._h, _dp(den)), "estimator_denominator")
-        return den.reshape(self.n_k1, self.n_mu, self.n_t, self.n_lm)
+        return den.reshape(self.out_shape(1)[1:])
 
     def combo_table(self):
         n = self.n_combos
@@ -299,17 +357,35 @@ class Plan:
 STAGES = ["forward", "step1", "step2", "reduce", "bin"]
 
 
+def stats_update(B, count, mean, m2, stream=None):
+    """estimator_stats_update: Welford update of (count, mean, m2) [n] with the
+    fields of B [batch][n] (CUDA float64 / int64 tensors)."""
+    n = mean.numel()
+    if B.dtype.itemsize != 8 or not (B.is_cuda and B.is_contiguous()) or B.numel() % max(n, 1):
+        raise ValueError("B must be a contiguous CUDA float64 tensor [batch][n]")
+    st = load().estimator_stats_update(C.c_void_p(B.data_ptr()), B.numel() // max(n, 1), n,
+                                       C.c_void_p(count.data_ptr()), C.c_void_p(mean.data_ptr()),
+                                       C.c_void_p(m2.data_ptr()), _stream_handle(stream))
+    _check(st, "estimator_stats_update")
+
+
 def status_string(status: int) -> str:
     return load().estimator_status_string(status).decode()
 
 
-def try_plan(n_g, box_len, k1_edges, n_mu, n_t, l_max, precision="mixed", max_batch=1):
+def try_plan(n_g, box_len, k1_edges, n_mu, n_t, l_max, precision="mixed", max_batch=1, n_mu_l=None, n_t_l=None):
     """Call estimator_plan and return (status, last_error); destroys any plan.
-    Used to check argument validation."""
+    Used to check argument validation (n_mu_l, n_t_l: raw per-l lists)."""
     lib = load()
     e = np.ascontiguousarray(k1_edges, dtype=np.float64)
     d = Desc(n_g, box_len, len(e) - 1, _dp(e), n_mu, n_t, l_max, PRECISIONS.get(precision, precision),
              max_batch)
+    keep = []
+    for name, vals in (("n_mu_l", n_mu_l), ("n_t_l", n_t_l)):
+        if vals is not None:
+            arr = (C.c_int * len(vals))(*vals)
+            keep.append(arr)
+            setattr(d, name, C.cast(arr, C.POINTER(C.c_int)))
     h = C.c_void_p()
     st = lib.estimator_plan(C.byref(h), C.byref(d), C.c_void_p(0))
     if h.value:

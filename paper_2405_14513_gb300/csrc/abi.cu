@@ -207,6 +207,11 @@ int check_desc(const bisp_desc *d)
     if (d->n_mu < 1 || d->n_t < 1 || d->n_mu > 4096 || d->n_t > 4096)
         return fail(BISP_INVALID_ARG, "n_mu and n_t must be in [1, 4096]");
     if (d->l_max < 0 || d->l_max > 8 || (d->l_max & 1)) return fail(BISP_INVALID_ARG, "l_max must be even, 0..8");
+    if (!d->n_mu_l != !d->n_t_l) return fail(BISP_INVALID_ARG, "give both n_mu_l and n_t_l, or neither");
+    if (d->n_mu_l)
+        for (int i = 0; i <= d->l_max / 2; ++i)
+            if (d->n_mu_l[i] < 1 || d->n_t_l[i] < 1 || d->n_mu_l[i] > 4096 || d->n_t_l[i] > 4096)
+                return fail(BISP_INVALID_ARG, "per-l (mu, t) bins must be in [1, 4096]");
     if (d->precision < BISP_PREC_FP32 || d->precision > BISP_PREC_MIXED_TC)
         return fail(BISP_INVALID_ARG, "unknown precision");
     if (d->max_batch < 1 || d->max_batch > 65535) return fail(BISP_INVALID_ARG, "max_batch must be in [1, 65535]");
@@ -422,10 +427,19 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     P.desc = *desc;
     P.k1_edges.assign(desc->k1_edges, desc->k1_edges + desc->n_k1 + 1);
     P.desc.k1_edges = P.k1_edges.data();
+    // per-l grids: the plan's own n_mu x n_t (combination bins) is that of l = 0
+    std::vector<int> mu_l, t_l;
+    if (desc->n_mu_l) {
+        mu_l.assign(desc->n_mu_l, desc->n_mu_l + desc->l_max / 2 + 1);
+        t_l.assign(desc->n_t_l, desc->n_t_l + desc->l_max / 2 + 1);
+        P.desc.n_mu = mu_l[0];
+        P.desc.n_t = t_l[0];
+    }
+    P.desc.n_mu_l = P.desc.n_t_l = nullptr;    // caller memory is not kept
     P.kf = kTwoPi / desc->box_len;
     P.volume = desc->box_len * desc->box_len * desc->box_len;
     P.n_lm = (desc->l_max / 2 + 1) * (desc->l_max / 2 + 1);
-    P.n_bins = int64_t(desc->n_k1) * desc->n_mu * desc->n_t;
+    P.n_bins = int64_t(desc->n_k1) * P.desc.n_mu * P.desc.n_t;
     p->precision = desc->precision;
     p->celem = desc->precision == BISP_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     if (!build_rings(desc->n_g, P.rings)) return fail(BISP_UNSUPPORTED_SIZE, "ring table");
@@ -485,6 +499,8 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->x_chunk = kXChunk;
     std::string err = enumerate(P, p->x_chunk);
     if (!err.empty()) return fail(BISP_INTERNAL, err);
+    unit_costs(P, p->x_chunk);
+    build_views(P, mu_l.empty() ? nullptr : mu_l.data(), t_l.empty() ? nullptr : t_l.data());
     sort_records(P);
 
     st = upload(p, &p->d_groups, P.groups, s);
@@ -498,7 +514,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
     if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
-    if (!st) st = dev_alloc(p, &p->d_den, size_t(P.n_bins) * P.n_lm);
+    if (!st) st = dev_alloc(p, &p->d_den, size_t(P.n_out));
     if (st) return st;
     // plan-time denominators of Eq. bs_lm2_1 (FP64)
     {
@@ -511,10 +527,11 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
         d_nt = static_cast<double *>(q);
         cudaError_t e = cudaMemcpyAsync(d_nt, P.rec_ntri.data(), P.rec_ntri.size() * sizeof(double),
                                         cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess)
-            e = launch_epilogue<double>(1, p->d_rec, p->d_bin_start, P.n_bins, d_nt, desc->l_max, nullptr, 1.0,
-                                        p->d_den, Batch{}, s);
-        p->h_den.resize(size_t(P.n_bins) * P.n_lm);
+        for (const View &v : P.views)
+            if (e == cudaSuccess)
+                e = launch_epilogue<double>(1, p->d_rec, p->d_bin_start + v.bs_off, v.n_bins, d_nt, v.l_lo, v.l_hi,
+                                            nullptr, 1.0, p->d_den + v.out_off, Batch{}, s);
+        p->h_den.resize(size_t(P.n_out));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->h_den.data(), p->d_den, p->h_den.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -557,19 +574,16 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
 }
 
 // Step-II launches of one estimate (one per non-empty block class)
-int step2_launches(const HostPlan &P)
+int step2_launches(const int64_t *lo, const int64_t *hi)
 {
     int n = 0;
-    if (P.tensor) {
-        for (int c = 0; c < kTcClasses; ++c) n += P.tc_class_begin[c + 1] > P.tc_class_begin[c];
-    } else {
-        for (int c = 2; c <= 4; ++c) n += P.class_begin[c + 1] > P.class_begin[c];
-    }
+    for (int c = 0; c < kClassSlots; ++c) n += hi[c] > lo[c];
     return n;
 }
 
 template <typename R, typename A, typename S, typename W>
-int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, double *B, cudaStream_t s)
+int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, double *B, int share, int nshares,
+                 cudaStream_t s)
 {
     using C = typename Cx<R>::T;
     const HostPlan &P = p->hp;
@@ -593,7 +607,7 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     const unsigned nf = unsigned(batch);
     const Batch in_field{nf, int64_t(ng2) * ng * int64_t(sizeof(R)), fs};   // input field -> region
     const Batch region{nf, fs, fs};
-    const Batch to_out{nf, fs, int64_t(P.n_bins) * P.n_lm * int64_t(sizeof(double))};
+    const Batch to_out{nf, fs, P.n_out * int64_t(sizeof(double))};
     {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
         StageMark m(p, BISP_STAGE_FORWARD, 3, s);
         CK(launch_fft_z_real<R>(delta, A_, ng, ng2, Rg.nz + 1, tw, in_field, s, p->rt_z));
@@ -611,16 +625,28 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
                                     p->rt_rows[L.lev]));
         }
     }
-    {   // Step II: triple sums (Eq. fftbs)
-        StageMark m(p, BISP_STAGE_STEP2, step2_launches(P), s);
+    {   // Step II: triple sums (Eq. fftbs), all units or one share of them
+        int64_t lo[kClassSlots], hi[kClassSlots];
+        const int64_t *cb;
+        const int ncls = unit_classes(P, &cb);
+        for (int c = 0; c < kClassSlots; ++c) lo[c] = hi[c] = 0;
+        if (nshares == 1) {
+            for (int c = 0; c < ncls; ++c) { lo[c] = cb[c]; hi[c] = cb[c + 1]; }
+        } else {
+            part_ranges(P, share, nshares, lo, hi);
+            // the partial sums of the other shares' units count as zero
+            for (unsigned f = 0; f < nf; ++f)
+                CK(cudaMemsetAsync(ws + int64_t(f) * fs + p->off_part, 0, size_t(P.n_partials) * sizeof(double), s));
+        }
+        StageMark m(p, BISP_STAGE_STEP2, step2_launches(lo, hi), s);
         if constexpr (sizeof(R) == 4) {
             if (P.tensor) {
-                CK(launch_step2_tc(atc, dstore, P.tc_class_begin, int(nf), s));
+                CK(launch_step2_tc(atc, dstore, lo, hi, int(nf), s));
             } else {
-                CK(launch_step2<R>(a2, dstore, P.class_begin, int(nf), s));
+                CK(launch_step2<R>(a2, dstore, lo, hi, int(nf), s));
             }
         } else {
-            CK(launch_step2<R>(a2, dstore, P.class_begin, int(nf), s));
+            CK(launch_step2<R>(a2, dstore, lo, hi, int(nf), s));
         }
     }
     {
@@ -629,26 +655,31 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
         CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, region, s));
     }
     {   // binning and the ratio of Eq. bs_lm2_1
-        StageMark m(p, BISP_STAGE_BIN, 1, s);
-        CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start, P.n_bins, Ssum, P.desc.l_max, p->d_den,
-                              1.0 / (P.volume * double(ng2)), B, to_out, s,
-                              p->precision != BISP_PREC_FP64));
+        StageMark m(p, BISP_STAGE_BIN, int(P.views.size()), s);
+        for (const View &v : P.views)
+            CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start + v.bs_off, v.n_bins, Ssum, v.l_lo, v.l_hi,
+                                  p->d_den + v.out_off, 1.0 / (P.volume * double(ng2)), B + v.out_off, to_out, s,
+                                  p->precision != BISP_PREC_FP64));
     }
     p->last_field = batch - 1;
     return BISP_OK;
 }
 
-int dispatch_estimate(bisp_plan *p, const void *delta, int batch, void *ws, double *B, cudaStream_t s)
+int dispatch_estimate(bisp_plan *p, const void *delta, int batch, void *ws, double *B, cudaStream_t s,
+                      int part = 0, int nparts = 1)
 {
     unsigned char *w = static_cast<unsigned char *>(ws);
     switch (p->precision) {
     case BISP_PREC_FP32:
-        return run_estimate<float, float, float, float>(p, static_cast<const float *>(delta), batch, w, B, s);
+        return run_estimate<float, float, float, float>(p, static_cast<const float *>(delta), batch, w, B, part,
+                                                        nparts, s);
     case BISP_PREC_MIXED:
     case BISP_PREC_MIXED_TC:
-        return run_estimate<float, float, double, double>(p, static_cast<const float *>(delta), batch, w, B, s);
+        return run_estimate<float, float, double, double>(p, static_cast<const float *>(delta), batch, w, B, part,
+                                                          nparts, s);
     default:
-        return run_estimate<double, double, double, double>(p, static_cast<const double *>(delta), batch, w, B, s);
+        return run_estimate<double, double, double, double>(p, static_cast<const double *>(delta), batch, w, B,
+                                                            part, nparts, s);
     }
 }
 
@@ -701,6 +732,24 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->dstore_bytes = size_t(P.dstore_elems) * p->celem;
     info->workspace_bytes = p->region_bytes;
     info->resident_bytes = p->resident;
+    info->n_views = int(P.views.size());
+    info->out_doubles = P.n_out;
+    return BISP_OK;
+}
+
+int estimator_view_info(const bisp_plan *p, int view, bisp_view_info *info)
+{
+    if (!p || !info) return fail(BISP_INVALID_ARG, "NULL argument");
+    const HostPlan &P = p->hp;
+    if (view < 0 || view >= int(P.views.size())) return fail(BISP_INVALID_ARG, "view out of range");
+    const View &v = P.views[view];
+    info->l_lo = v.l_lo;
+    info->l_hi = v.l_hi;
+    info->n_mu = v.n_mu;
+    info->n_t = v.n_t;
+    info->n_lm = v.n_lm;
+    info->n_bins = v.n_bins;
+    info->offset = v.out_off;
     return BISP_OK;
 }
 
@@ -719,6 +768,27 @@ int estimator_estimate(bisp_plan *p, const void *delta, int batch, void *workspa
     return dispatch_estimate(p, delta, batch, workspace, B, static_cast<cudaStream_t>(stream));
 }
 
+int estimator_stats_update(const double *B, int batch, int64_t n, int64_t *count, double *mean, double *m2,
+                           void *stream)
+{
+    g_err.clear();
+    if (!B || !count || !mean || !m2) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 0 || n < 0) return fail(BISP_INVALID_ARG, "batch and n must be >= 0");
+    CK(launch_stats_update(B, batch, n, count, mean, m2, static_cast<cudaStream_t>(stream)));
+    return BISP_OK;
+}
+
+int estimator_estimate_part(bisp_plan *p, const void *delta, int batch, void *workspace, double *B_part, int part,
+                            int nparts, void *stream)
+{
+    g_err.clear();
+    if (!p || !delta || !workspace || !B_part) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    if (nparts < 1 || part < 0 || part >= nparts) return fail(BISP_INVALID_ARG, "part must satisfy 0 <= part < nparts");
+    if (reinterpret_cast<uintptr_t>(workspace) % 256) return fail(BISP_INVALID_ARG, "workspace not 256-byte aligned");
+    return dispatch_estimate(p, delta, batch, workspace, B_part, static_cast<cudaStream_t>(stream), part, nparts);
+}
+
 int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, double *B_host, void *stream)
 {
     g_err.clear();
@@ -728,7 +798,7 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
     const HostPlan &P = p->hp;
     const size_t field = size_t(P.desc.n_g) * P.desc.n_g * P.desc.n_g *
                          (p->precision == BISP_PREC_FP64 ? sizeof(double) : sizeof(float));
-    const size_t outb = size_t(P.n_bins) * P.n_lm * sizeof(double);
+    const size_t outb = size_t(P.n_out) * sizeof(double);
     if (!p->own_ws) {
         CK(cudaMalloc(&p->own_ws, std::max<size_t>(size_t(P.desc.max_batch) * p->region_bytes, 256)));
         CK(cudaMalloc(&p->own_in, field * P.desc.max_batch));
@@ -863,7 +933,8 @@ int estimator_stage_flops(const bisp_plan *p, double *flops)
     flops[BISP_STAGE_STEP1] = s1;
     flops[BISP_STAGE_STEP2] = 4.0 * P.triple_products + 6.0 * P.pair_products;
     flops[BISP_STAGE_REDUCE] = double(P.n_partials);
-    flops[BISP_STAGE_BIN] = double(P.n_combos) * 4.0 * P.n_lm;
+    flops[BISP_STAGE_BIN] = 0;
+    for (const View &v : P.views) flops[BISP_STAGE_BIN] += double(P.n_combos) * 4.0 * (v.l_hi / 2 + 1) * (v.l_hi / 2 + 1);
     return BISP_OK;
 }
 

@@ -409,12 +409,14 @@ __constant__ double c_rec[2][9][9];
 
 // W: type of the sums over records; Y: type the Y_lm of each record are
 // computed in (FP32 for the FP32-transform paths, whose tolerance is 1e-4;
-// FP64 for the FP64 path and the plan-time denominators).
+// FP64 for the FP64 path and the plan-time denominators).  The moments
+// written are lm_lo .. (LMAX/2 + 1)^2 - 1 (even l from l_lo = 2 sqrt(lm_lo)),
+// nlm_out = that count per bin, for out and den alike.
 template <typename W, typename Y, int LMAX>
 __global__ void __launch_bounds__(256)
 k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ bin_start, int64_t nbins,
            const double *__restrict__ value, const double *__restrict__ den, double norm,
-           double *__restrict__ out, int64_t fs_in, int64_t fs_out)
+           double *__restrict__ out, int64_t fs_in, int64_t fs_out, int lm_lo, int nlm_out)
 {
     value = field_ptr(value, fs_in);
     out = field_ptr(out, fs_out);
@@ -468,17 +470,42 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
     for (int i = 0; i < NLM; ++i) {
         W v = acc[i];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) {
+        if (lane == 0 && i >= lm_lo) {
+            const int64_t o = b * nlm_out + (i - lm_lo);
             if (mode == 0) {
                 int l = 0;
                 while ((l / 2 + 1) * (l / 2 + 1) <= i) l += 2;
-                const double d = den[b * NLM + i];
-                out[b * NLM + i] = d > 0.0 ? c_pref[l] * double(v) * norm / d : __longlong_as_double(0x7ff8000000000000LL);
+                const double d = den[o];
+                out[o] = d > 0.0 ? c_pref[l] * double(v) * norm / d : __longlong_as_double(0x7ff8000000000000LL);
             } else {
-                out[b * NLM + i] = double(v);
+                out[o] = double(v);
             }
         }
     }
+}
+
+// Running statistics of estimates over fields: Welford's update (mean and
+// sum of squared deviations, FP64) of element i with B[f][i], f < nf, in
+// field order; non-finite values (empty bins) are skipped.
+__global__ void __launch_bounds__(256)
+k_stats_update(const double *__restrict__ B, int nf, int64_t n, int64_t *__restrict__ count,
+               double *__restrict__ mean, double *__restrict__ m2)
+{
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = count[i];
+    double m = mean[i], s = m2[i];
+    for (int f = 0; f < nf; ++f) {
+        const double x = B[int64_t(f) * n + i];
+        if (!isfinite(x)) continue;
+        ++c;
+        const double d = x - m;
+        m += d / double(c);
+        s += d * (x - m);
+    }
+    count[i] = c;
+    mean[i] = m;
+    m2[i] = s;
 }
 
 __global__ void __launch_bounds__(256)
@@ -577,27 +604,22 @@ cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dst
 }
 
 template <typename R>
-cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
+cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *lo, const int64_t *hi,
                          int nf, cudaStream_t s)
 {
     if constexpr (sizeof(R) == 4) {
-        cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                                 kStep2ClassSmem[2], nf, s);
+        cudaError_t e = launch_step2_class<R, 4>(a, dstore, lo[2], hi[2] - lo[2], kStep2ClassSmem[2], nf, s);
         if (e == cudaSuccess)
-            e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                         kStep2ClassSmem[3], nf, s);
+            e = launch_step2_class<R, 8>(a, dstore, lo[3], hi[3] - lo[3], kStep2ClassSmem[3], nf, s);
         if (e == cudaSuccess)
-            e = launch_step2_class<R, 16>(a, dstore, class_begin[4], class_begin[5] - class_begin[4],
-                                          kStep2ClassSmem[4], nf, s);
+            e = launch_step2_class<R, 16>(a, dstore, lo[4], hi[4] - lo[4], kStep2ClassSmem[4], nf, s);
         return e;
     }
     // FP64: register tiles, blocks of at most 8 warps (register file)
-    cudaError_t e = launch_step2_class<R, 4>(a, dstore, class_begin[2], class_begin[3] - class_begin[2],
-                                             kStep2ClassSmem[2], nf, s);
+    cudaError_t e = launch_step2_class<R, 4>(a, dstore, lo[2], hi[2] - lo[2], kStep2ClassSmem[2], nf, s);
     if (e == cudaSuccess)
-        e = launch_step2_class<R, 8>(a, dstore, class_begin[3], class_begin[4] - class_begin[3],
-                                     kStep2ClassSmem[3], nf, s);
-    if (e == cudaSuccess && class_begin[5] != class_begin[4]) e = cudaErrorInvalidValue;
+        e = launch_step2_class<R, 8>(a, dstore, lo[3], hi[3] - lo[3], kStep2ClassSmem[3], nf, s);
+    if (e == cudaSuccess && hi[4] != lo[4]) e = cudaErrorInvalidValue;
     return e;
 }
 
@@ -612,16 +634,18 @@ cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const d
 
 template <typename W, typename Y>
 cudaError_t epilogue_lmax(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins, const double *value,
-                          int l_max, const double *den, double norm, double *out, const Batch &fb, cudaStream_t s)
+                          int l_lo, int l_hi, const double *den, double norm, double *out, const Batch &fb,
+                          cudaStream_t s)
 {
     const dim3 grid(unsigned((nbins * 32 + 255) / 256), fb.nf);
     const int64_t fi = fb.fs_in, fo = fb.fs_out;
-    switch (l_max) {
-    case 0: k_epilogue<W, Y, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 2: k_epilogue<W, Y, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 4: k_epilogue<W, Y, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 6: k_epilogue<W, Y, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
-    case 8: k_epilogue<W, Y, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo); break;
+    const int lo = (l_lo / 2) * (l_lo / 2), n = (l_hi / 2 + 1) * (l_hi / 2 + 1) - lo;
+    switch (l_hi) {
+    case 0: k_epilogue<W, Y, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
+    case 2: k_epilogue<W, Y, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
+    case 4: k_epilogue<W, Y, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
+    case 6: k_epilogue<W, Y, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
+    case 8: k_epilogue<W, Y, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -629,13 +653,14 @@ cudaError_t epilogue_lmax(int mode, const Record *rec, const int64_t *bin_start,
 
 template <typename W>
 cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
-                            const double *value, int l_max, const double *den, double norm, double *out,
+                            const double *value, int l_lo, int l_hi, const double *den, double norm, double *out,
                             const Batch &fb, cudaStream_t s, bool fp32_weights)
 {
     if (nbins == 0) return cudaSuccess;
+    if (l_lo < 0 || l_lo > l_hi || (l_lo & 1)) return cudaErrorInvalidValue;
     if (fp32_weights)
-        return epilogue_lmax<W, float>(mode, rec, bin_start, nbins, value, l_max, den, norm, out, fb, s);
-    return epilogue_lmax<W, W>(mode, rec, bin_start, nbins, value, l_max, den, norm, out, fb, s);
+        return epilogue_lmax<W, float>(mode, rec, bin_start, nbins, value, l_lo, l_hi, den, norm, out, fb, s);
+    return epilogue_lmax<W, W>(mode, rec, bin_start, nbins, value, l_lo, l_hi, den, norm, out, fb, s);
 }
 
 // Every kernel that takes more than 48 KB of dynamic shared memory is
@@ -662,6 +687,14 @@ cudaError_t init_kernel_attributes()
     set((const void *)k_step2<double, 4>);
     set((const void *)k_step2<double, 8>);
     return e;
+}
+
+cudaError_t launch_stats_update(const double *B, int nf, int64_t n, int64_t *count, double *mean, double *m2,
+                                cudaStream_t s)
+{
+    if (n == 0 || nf == 0) return cudaSuccess;
+    k_stats_update<<<unsigned((n + 255) / 256), 256, 0, s>>>(B, nf, n, count, mean, m2);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32_t *triples, int64_t ntriples,
@@ -694,11 +727,15 @@ template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int
 template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
-template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, int, cudaStream_t);
-template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, int, cudaStream_t);
+template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, const int64_t *, int,
+                                         cudaStream_t);
+template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, const int64_t *, int,
+                                          cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
 template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
-template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t, bool);
-template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, const double *, double, double *, const Batch &, cudaStream_t, bool);
+template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, int,
+                                            const double *, double, double *, const Batch &, cudaStream_t, bool);
+template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, int,
+                                             const double *, double, double *, const Batch &, cudaStream_t, bool);
 
 }  // namespace bisp

@@ -87,11 +87,12 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
                                typename Cx<R>::T *gt, const Twiddles<typename Cx<R>::T> &tw,
                                const Batch &fb, cudaStream_t s, int rt = 0);
 
-// Step II: partial triple sums of every unit, one block per unit, one launch
-// per block class (units [class_begin[c], class_begin[c+1]) run in blocks of
-// 2^c warps with kStep2ClassSmem[c] bytes of shared memory).
+// Step II: partial triple sums of units, one block per unit, one launch per
+// block class (units [lo[c], hi[c]) run in blocks of 2^c warps with
+// kStep2ClassSmem[c] bytes of shared memory; a whole estimate passes
+// lo = class_begin, hi = class_begin + 1).
 template <typename R>
-cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *class_begin,
+cudaError_t launch_step2(const StepIIArgs &a, const typename Cx<R>::T *dstore, const int64_t *lo, const int64_t *hi,
                          int nf, cudaStream_t s);
 
 // Step II on tcgen05 (FP32 fields; step2_tc.cu).
@@ -108,9 +109,9 @@ struct TcArgs {
     int64_t fs;              // bytes between the workspace regions of the fields of a batch
 };
 
-// One launch per column class: units [class_begin[c], class_begin[c+1]),
-// one block per unit with kTcSmem bytes of shared memory.
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *class_begin, int nf,
+// One launch per column class: units [lo[c], hi[c]), one block per unit
+// with kTcSmem bytes of shared memory.
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *lo, const int64_t *hi, int nf,
                             cudaStream_t s);
 
 // Allow the kernels their dynamic shared memory once (kernels.cu and
@@ -123,16 +124,22 @@ template <typename A>
 cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const double *partials,
                                    int ng, double *S, const Batch &fb, cudaStream_t s);
 
-// Binning epilogue of Eq. bs_lm2_1.  mode 0: B = sqrt((2l+1)/4pi) num /
-// (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
+// Binning epilogue of Eq. bs_lm2_1 for the moments of even l_lo .. l_hi
+// (out and den: [nbins][moments of those l]).  mode 0: B = sqrt((2l+1)/4pi)
+// num / (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
 // fp32_weights: the Y_lm of each record in FP32 (sums stay in W).
 template <typename W>
 cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
-                            const double *value, int l_max, const double *den, double norm,
+                            const double *value, int l_lo, int l_hi, const double *den, double norm,
                             double *out, const Batch &fb, cudaStream_t s, bool fp32_weights = false);
 
 // Y_lm normalisations nlm[l][m] and the prefactors sqrt((2l+1)/(4 pi)).
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);
+
+// Welford update of per-element count, mean and squared deviations with
+// nf fields B[f][0 .. n-1] (non-finite values skipped).
+cudaError_t launch_stats_update(const double *B, int nf, int64_t n, int64_t *count, double *mean, double *m2,
+                                cudaStream_t s);
 
 // N_tri of unordered ring triples from the unit fields (Eq. Ntri2), FP64.
 // triples[4 t .. 4 t + 3] = (r1, r2, r3, level index into grids.M).

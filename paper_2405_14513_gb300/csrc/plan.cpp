@@ -72,10 +72,22 @@ int triple_level(const Rings &R, int r1, int r2, int r3)
 namespace {
 
 struct Geo {
-    int bin;
+    int bin;                   // (k1, mu, t) bin on the plan's n_mu x n_t grid
     int degenerate;
     double pz, cphi;
+    int ib;                    // k1 bin
+    double mu, t;              // shape (mu clamped to [1/2, 1])
 };
+
+// (k1, mu, t) bin of a shape on an n_mu x n_t grid of [1/2, 1]^2 (top edges closed)
+int grid_bin(int ib, double mu, double t, int n_mu, int n_t)
+{
+    int it = int(std::floor((t - 0.5) * (2.0 * n_t)));
+    int im = int(std::floor((mu - 0.5) * (2.0 * n_mu)));
+    if (it >= n_t) it = n_t - 1;
+    if (im >= n_mu) im = n_mu - 1;
+    return (ib * n_mu + im) * n_t + it;
+}
 
 // Acceptance and geometry of one combination (planes n1, n2, n3 with ring
 // radii kp1..kp3 in grid units): K1 >= K2 >= K3 > 0 with
@@ -103,11 +115,10 @@ bool combo_geometry(const HostPlan &P, double kp1, double kp2, double kp3, int n
     if (mu > 1.0) mu = 1.0;
     if (mu < 0.5) mu = 0.5;
     if (t < 0.5) return false;
-    int it = int(std::floor((t - 0.5) * (2.0 * d.n_t)));
-    int im = int(std::floor((mu - 0.5) * (2.0 * d.n_mu)));
-    if (it >= d.n_t) it = d.n_t - 1;
-    if (im >= d.n_mu) im = d.n_mu - 1;
-    g->bin = (ib * d.n_mu + im) * d.n_t + it;
+    g->bin = grid_bin(ib, mu, t, d.n_mu, d.n_t);
+    g->ib = ib;
+    g->mu = mu;
+    g->t = t;
     double mu1 = double(n1) / s1;
     double mu2 = double(n2) / s2;
     g->pz = mu1;
@@ -599,11 +610,42 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     return "";
 }
 
+void build_views(HostPlan &P, const int *n_mu_l, const int *n_t_l)
+{
+    const bisp_desc &d = P.desc;
+    P.views.clear();
+    for (int l = 0; l <= d.l_max; l += 2) {
+        const int nm = n_mu_l ? n_mu_l[l / 2] : d.n_mu, nt = n_t_l ? n_t_l[l / 2] : d.n_t;
+        if (!P.views.empty() && P.views.back().n_mu == nm && P.views.back().n_t == nt) {
+            P.views.back().l_hi = l;
+            continue;
+        }
+        View v;
+        v.l_lo = v.l_hi = l;
+        v.n_mu = nm;
+        v.n_t = nt;
+        P.views.push_back(v);
+    }
+    int64_t off = 0, bs = 0;
+    for (size_t i = 0; i < P.views.size(); ++i) {
+        View &v = P.views[i];
+        v.lm_lo = (v.l_lo / 2) * (v.l_lo / 2);
+        v.n_lm = (v.l_hi / 2 + 1) * (v.l_hi / 2 + 1) - v.lm_lo;
+        v.n_bins = int64_t(d.n_k1) * v.n_mu * v.n_t;
+        v.out_off = off;
+        v.bs_off = bs;
+        off += v.n_bins * v.n_lm;
+        bs += v.n_bins + 1;
+    }
+    P.n_out = off;
+}
+
 void sort_records(HostPlan &P)
 {
-    // bin of each record, recomputed from S order through its group
-    const int64_t nb = P.n_bins;
-    std::vector<int32_t> bin(P.records_s.size());
+    // shape of each record, recomputed from S order through its group
+    const size_t n = P.records_s.size();
+    std::vector<int32_t> bin(n), kb(n);
+    std::vector<double> mu(n), t(n);
     const Rings &R = P.rings;
     for (const auto &G : P.groups)
         for (int s = 0; s < G.nrow; ++s) {
@@ -611,23 +653,83 @@ void sort_records(HostPlan &P)
             for (int j = 0; j < rw.n; ++j) {
                 Geo g;
                 combo_geometry(P, R.kperp[rw.r1], R.kperp[rw.r2], R.kperp[rw.r3a + j], G.n1, G.n2, G.n3, &g);
-                bin[G.c0 + rw.coff + j] = g.bin;
+                const int64_t k = G.c0 + rw.coff + j;
+                bin[k] = g.bin;
+                kb[k] = g.ib;
+                mu[k] = g.mu;
+                t[k] = g.t;
             }
         }
     P.combo_bin = bin;
-    P.bin_start.assign(nb + 1, 0);
-    for (auto b : bin) P.bin_start[b + 1]++;
-    for (int64_t b = 0; b < nb; ++b) P.bin_start[b + 1] += P.bin_start[b];
-    std::vector<int64_t> pos(P.bin_start.begin(), P.bin_start.end() - 1);
-    P.records.resize(P.records_s.size());
-    P.rec_ntri.resize(P.records_s.size());
-    for (size_t k = 0; k < P.records_s.size(); ++k) {
-        int64_t p = pos[bin[k]]++;
-        P.records[p] = P.records_s[k];
-        P.rec_ntri[p] = P.ntri_s[k];
+    size_t total_bs = 0;
+    for (const View &v : P.views) total_bs += size_t(v.n_bins) + 1;
+    P.records.resize(n * P.views.size());
+    P.rec_ntri.resize(n * P.views.size());
+    P.bin_start.assign(total_bs, 0);
+    for (size_t vi = 0; vi < P.views.size(); ++vi) {
+        View &v = P.views[vi];
+        v.rec_off = int64_t(vi * n);
+        for (size_t k = 0; k < n; ++k) bin[k] = grid_bin(kb[k], mu[k], t[k], v.n_mu, v.n_t);
+        int64_t *bs = P.bin_start.data() + v.bs_off;
+        bs[0] = v.rec_off;
+        for (size_t k = 0; k < n; ++k) bs[bin[k] + 1]++;
+        for (int64_t b = 0; b < v.n_bins; ++b) bs[b + 1] += bs[b];
+        std::vector<int64_t> pos(bs, bs + v.n_bins);
+        for (size_t k = 0; k < n; ++k) {
+            const int64_t p = pos[bin[k]]++;
+            P.records[p] = P.records_s[k];
+            P.rec_ntri[p] = P.ntri_s[k];
+        }
     }
     std::vector<Record>().swap(P.records_s);
     std::vector<double>().swap(P.ntri_s);
+}
+
+int unit_classes(const HostPlan &P, const int64_t **class_begin)
+{
+    *class_begin = P.tensor ? P.tc_class_begin : P.class_begin;
+    return P.tensor ? kTcClasses : 5;
+}
+
+void unit_costs(HostPlan &P, int64_t x_chunk)
+{
+    auto points = [&](int M, int chunk) {
+        const int64_t m2 = int64_t(M) * M, x0 = int64_t(chunk) * x_chunk;
+        return double(std::min(x_chunk, m2 - x0));
+    };
+    const size_t n = P.tensor ? P.tc_units.size() : P.units.size();
+    P.unit_cost.assign(n + 1, 0.0);
+    for (size_t u = 0; u < n; ++u) {
+        double c;
+        if (P.tensor) {
+            const TcUnit &U = P.tc_units[u];
+            c = points(P.tc_tiles[U.tile].M, U.chunk);
+        } else {
+            const Unit &U = P.units[u];
+            c = points(P.groups[U.group].M, U.chunk) * U.nt;
+        }
+        P.unit_cost[u + 1] = P.unit_cost[u] + c;
+    }
+}
+
+void part_ranges(const HostPlan &P, int part, int nparts, int64_t *lo, int64_t *hi)
+{
+    const int64_t *cb;
+    const int ncls = unit_classes(P, &cb);
+    const std::vector<double> &c = P.unit_cost;
+    for (int k = 0; k < ncls; ++k) {
+        const int64_t a = cb[k], b = cb[k + 1];
+        // first unit of share p: the first whose preceding cost reaches p/nparts of the class
+        auto cut = [&](int p) -> int64_t {
+            if (p <= 0) return a;
+            if (p >= nparts) return b;
+            const double target = c[a] + (c[b] - c[a]) * double(p) / double(nparts);
+            return int64_t(std::lower_bound(c.begin() + a, c.begin() + b, target) - c.begin());
+        };
+        lo[k] = cut(part);
+        hi[k] = cut(part + 1);
+    }
+    for (int k = ncls; k < kClassSlots; ++k) lo[k] = hi[k] = 0;
 }
 
 }  // namespace bisp

@@ -157,6 +157,19 @@ struct Record {
     double cphi;               // cos(phi) of p
 };
 
+// A binning of the combinations (Eq. bs_lm2_1): the moments of even l
+// l_lo .. l_hi on an n_mu x n_t grid of (mu, t) bins; one field's output
+// block [n_k1][n_mu][n_t][n_lm] starts at out_off doubles, its records in
+// (k1, mu, t)-bin order at rec_off of the plan's record array, its
+// bin_start at bs_off of the plan's bin_start array (absolute record
+// indices).  One view (every l on the caller's n_mu x n_t) unless per-l
+// bins are asked for; then consecutive l with the same grid share a view.
+struct View {
+    int l_lo = 0, l_hi = 0, n_mu = 1, n_t = 1;
+    int lm_lo = 0, n_lm = 1;           // first moment index (l_lo/2)^2, moments in the view
+    int64_t n_bins = 0, out_off = 0, rec_off = 0, bs_off = 0;
+};
+
 struct Level {
     int lev = 0;               // index into Rings::grid
     int M = 0;                 // grid side
@@ -192,6 +205,7 @@ struct HostPlan {
     int max_cls = 4;                    // largest block class (set before enumerate)
     size_t celem = 8;                   // bytes of a staged complex value (set before enumerate)
     int64_t class_begin[6] = {};        // units of class c: [class_begin[c], class_begin[c+1])
+    std::vector<double> unit_cost;      // prefix sums of the Step-II units' costs, launch order (n + 1)
     int64_t n_combos = 0;
     int64_t n_partials = 0;
     int64_t n_pairs = 0;
@@ -201,10 +215,12 @@ struct HostPlan {
     std::vector<Record> records_s;      // S order (moved to bin order later)
     std::vector<double> ntri_s;         // N_tri per combination, S order
 
-    // bin-sorted records
+    // binnings: records of every view in its own bin order, one after another
+    std::vector<View> views;
+    int64_t n_out = 0;                  // doubles of one field's output (all views)
     std::vector<Record> records;
     std::vector<double> rec_ntri;
-    std::vector<int64_t> bin_start;     // n_bins + 1
+    std::vector<int64_t> bin_start;     // per view: n_bins + 1 absolute record indices
 
     // D store: offset (in complex elements) of field (level, plane, ring),
     // -1 where not stored; [kMaxLevels][nz+1][kMaxRings]
@@ -231,7 +247,26 @@ int triple_level(const Rings &R, int r1, int r2, int r3);
 // Requires rings and ntri.  Returns "" or an error message.
 std::string enumerate(HostPlan &P, int64_t x_chunk);
 
-// Counting sort of the records by (k1, mu, t) bin.
+// Views of the plan (from desc n_mu, n_t, or the per-l grids n_mu_l, n_t_l
+// for l = 0, 2, .., l_max), their output offsets and n_out.
+void build_views(HostPlan &P, const int *n_mu_l, const int *n_t_l);
+
+// Counting sort of the records by (k1, mu, t) bin, once per view.
 void sort_records(HostPlan &P);
+
+// Step-II block classes of the plan's kernel (tcgen05: NC = 16, 32, 48, 64;
+// CUDA cores: 2^c warps, c = 2, 3, 4), as ranges of its launch-ordered units.
+constexpr int kClassSlots = 6;
+int unit_classes(const HostPlan &P, const int64_t **class_begin);
+
+// Fill P.unit_cost: the cost of a unit is the grid points of its x chunk
+// (tcgen05: one tile per block) times its register tiles (CUDA cores).
+void unit_costs(HostPlan &P, int64_t x_chunk);
+
+// Share `part` of `nparts` of the Step-II work: for every block class k,
+// the units [lo[k], hi[k]), a contiguous run of the class with about
+// 1/nparts of its cost.  The shares of parts 0 .. nparts - 1 partition
+// every class.
+void part_ranges(const HostPlan &P, int part, int nparts, int64_t *lo, int64_t *hi);
 
 }  // namespace bisp

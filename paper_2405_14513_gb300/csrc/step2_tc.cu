@@ -71,7 +71,25 @@ __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t b, uin
                  ::"r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// -hi(x): x with its 13 low mantissa bits cleared, negated (one logical operation)
+__device__ __forceinline__ uint32_t tf32_neg_hi(float x) { return (__float_as_uint(x) & 0xFFFFE000u) ^ 0x80000000u; }
+
+// (a, b) += (x, y): one packed FP32 addition (round to nearest, as two
+// scalar additions would be)
+__device__ __forceinline__ void add2(float &a, float &b, uint32_t x, uint32_t y)
+{
+    asm("{\n.reg .b64 p, q;\nmov.b64 p, {%0, %1};\nmov.b64 q, {%2, %3};\nadd.rn.f32x2 p, p, q;\nmov.b64 {%0, %1}, p;\n}\n"
+        : "+f"(a), "+f"(b) : "r"(x), "r"(y));
+}
+
+// (lo(x), lo(y)) = (x - hi(x), y - hi(y)), exact
+__device__ __forceinline__ void lo2(float x, float y, uint32_t &lx, uint32_t &ly)
+{
+    float a = x, b = y;
+    add2(a, b, tf32_neg_hi(x), tf32_neg_hi(y));
+    lx = __float_as_uint(a);
+    ly = __float_as_uint(b);
+}
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
 {
@@ -99,7 +117,7 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
         uint32_t v[8];
         tmem_ld8(tcol + 8 * q, v);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[8 * q + j] += __uint_as_float(v[j]);
+        for (int j = 0; j < 8; j += 2) add2(acc[8 * q + j], acc[8 * q + j + 1], v[j], v[j + 1]);
     }
 }
 
@@ -109,27 +127,29 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 //              one per lane): warp w forms grid points 0-7 of a stage and
 //              adds accumulator columns 0 .. NC/2 - 1 into FP32 registers,
 //              warp w + 4 points 8-15 and columns NC/2 .. NC - 1;
-//   warps 8-9  (one thread each) issue the MMAs: a tcgen05.mma holds its
-//              issuing thread for tens of cycles, so for NC <= 32 two
-//              issuers split the 12 MMAs of a stage, each into its own
-//              accumulator (tensor-memory columns 128 + 64 b + 32 i for
-//              stage buffer b, issuer i); for NC > 32 warp 4 issues all 12
-//              into columns 128 + 64 b.  Accumulators are double-buffered,
-//              so the MMAs of stage s wait only for stage s - 2's read;
-//   warps 10-11 stage the fields of each stage in shared memory (cp.async,
+//   warp 8     (one thread) issues the 12 MMAs of a stage into the
+//              accumulator of its buffer b (tensor-memory columns
+//              128 + 64 b).  Accumulators are double-buffered, so the MMAs
+//              of stage s wait only for stage s - 2's read.  (A second
+//              issuer with an accumulator of its own was slower: the compute
+//              warps, not the MMA issue, set the pace, and a second
+//              accumulator doubles their reads);
+//   warps 9-10 stage the fields of each stage in shared memory (cp.async,
 //              a ring of 3 to 8 stages).
 // mbarriers (phase k of a barrier = its k-th use):
 //   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
 //   empty[q]  ring buffer q has been read             (256 compute arrivals)
 //   aready[b] A and B (high, low) of buffer b written (256 compute arrivals)
-//   mdone[b][i] issuer i's MMAs into buffer b are done (commit)
+//   mdone[b]  the MMAs into buffer b are done         (commit)
 //   dfree[b]  accumulators of buffer b have been read (256 compute arrivals)
-constexpr int kThreads = 384;
+//   drain     every MMA the block issued is done      (commit; before the
+//             tensor memory is freed, also when the block gives up early)
+constexpr int kThreads = 352;
 constexpr int kCompute = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
-    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2][2], dfree[2];
+    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2], dfree[2], drain;
     uint32_t tmem;
     int abort;
 };
@@ -161,6 +181,19 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, vo
     return false;
 }
 
+// Bounded wait for phase `parity` of m that does not stop at the abort flag
+// (waits for the block's own tensor-core work).
+__device__ __forceinline__ void mbar_wait_bounded(uint64_t *m, uint32_t parity)
+{
+    const uint32_t a = su32(m);
+    for (int i = 0; i < kWaitSpins; ++i) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        if (ok) return;
+    }
+}
+
 // The A columns of half a stage (grid points 8 half .. 8 half + 7) for this
 // thread's row: P = D1' D2' with D' the stored field or its conjugate (G1,
 // G2: n1 < 0, n2 < 0), and A = (Re P, -g3 Im P) (G3: n3 < 0), high parts at
@@ -189,16 +222,19 @@ __device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned c
             e[2] = fmaf(u.z, v.z, NEG12 ? -t2 : t2);
             e[3] = fmaf(NEG2 ? -u.z : u.z, v.w, NEG1 ? -t3 : t3);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                hi[4 * k + j] = __float_as_uint(e[j]);
-                lo[4 * k + j] = __float_as_uint(e[j] - tf32_hi(e[j]));
-            }
+            for (int j = 0; j < 4; ++j) hi[4 * k + j] = __float_as_uint(e[j]);
+            lo2(e[0], e[1], lo[4 * k], lo[4 * k + 1]);
+            lo2(e[2], e[3], lo[4 * k + 2], lo[4 * k + 3]);
         }
         tmem_st8(a + 8 * h, hi);
         tmem_st8(a + 32 + 8 * h, lo);
     }
 }
 
+// Two blocks per SM (sharing its 227 KB of shared memory and 512
+// tensor-memory columns) hold 22 warps, 6 on some of the SM's four
+// schedulers, whose register files are 16384 each: at most 80 registers a
+// thread (an 88-register build ran one block per SM and was 45% slower).
 template <int NC>
 __global__ void __launch_bounds__(kThreads, 2)
 k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
@@ -208,7 +244,6 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     constexpr uint32_t SBO = 128;                // next 8 rows of B
     constexpr int BB = NC * kTX * 8;             // bytes of one stage of B
     constexpr uint32_t ID = idesc_tf32<NC>();
-    constexpr bool kTwoIssuers = NC <= 32;       // two accumulators of 32 columns fit a buffer
     extern __shared__ __align__(1024) unsigned char smem[];
 
     const TcUnit U = args.units[unit0 + blockIdx.x];
@@ -247,10 +282,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&sy->aready[b], kCompute);
-            mbar_init(&sy->mdone[b][0], 1);
-            mbar_init(&sy->mdone[b][1], 1);
+            mbar_init(&sy->mdone[b], 1);
             mbar_init(&sy->dfree[b], kCompute);
         }
+        mbar_init(&sy->drain, 1);
         sy->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
@@ -278,12 +313,12 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     const int nstage = int((x1 - x0) / kTX);
     bool ok = true;
 
-    if (warp >= 10) {
+    if (warp >= 9) {
         // producers: lane l of the 64 copies piece p = l % 8 (grid points
         // 2p, 2p + 1) of fields l / 8, l / 8 + 8, ...; their offsets (in
         // 16-element units: every stored field starts at a multiple of 16)
         // are held in registers
-        const int pl = t - 320, p = pl & 7, f0 = pl >> 3;
+        const int pl = t - 288, p = pl & 7, f0 = pl >> 3;
         uint32_t o16[kProdFields];
 #pragma unroll
         for (int k = 0; k < kProdFields; ++k) {
@@ -291,9 +326,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             const int64_t o = f < nf ? offs[f] : -1;
             o16[k] = o < 0 ? 0xFFFFFFFFu : uint32_t(o >> 4);
         }
+        int q = 0;                                   // ring buffer of stage st
+        uint32_t ph = 0;                             // its phase: (st / S) & 1
         for (int st = 0; st < nstage && ok; ++st) {
-            const int q = st % S;
-            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], uint32_t(st / S - 1) & 1, abort);
+            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], ph ^ 1u, abort);
             if (!ok) break;
             const float2 *src = dstore + x0 + int64_t(st) * kTX + 2 * p;
             const uint32_t dst = su32(sS + q * rowb + f0 * kSlotBytes + p * 16);
@@ -301,14 +337,13 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             for (int k = 0; k < kProdFields; ++k)
                 if (o16[k] != 0xFFFFFFFFu) cp_async16(dst + 8 * k * kSlotBytes, src + (int64_t(o16[k]) << 4));
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(&sy->full[q])) : "memory");
+            if (++q == S) { q = 0; ph ^= 1u; }
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
-    } else if (warp >= 8) {
-        // MMA issue.  NC <= 32: issuer 0 takes high A x high B over k-steps
-        // 0-3 and low A x high B over 0-1, issuer 1 low A x high B over 2-3
-        // and high A x low B over 0-3.  NC > 32: issuer 0 takes all 12.
-        const int me = warp - 8;
-        if (lane == 0 && (kTwoIssuers || me == 0)) {
+    } else if (warp == 8) {
+        // MMA issue: high A x high B, low A x high B and high A x low B over
+        // the four k-steps of the stage
+        if (lane == 0) {
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
             for (int st = 0; st < nstage && ok; ++st) {
                 const int b = st & 1;
@@ -317,26 +352,22 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a = tmem + 64 * b;
-                const uint32_t d = tmem + 128 + 64 * b + (kTwoIssuers ? 32 * me : 0);
+                const uint32_t d = tmem + 128 + 64 * b;
                 const uint64_t bo = uint64_t(b * BB) >> 4;      // start-address field offset of buffer b
                 constexpr uint64_t kstep = (2 * LBO) >> 4;      // next k-step (two core matrices along K)
-                if (me == 0) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dh + bo + j * kstep, ID, j > 0);
+                for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dh + bo + j * kstep, ID, j > 0);
 #pragma unroll
-                    for (int j = 0; j < (kTwoIssuers ? 2 : 4); ++j)
-                        mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
-                }
-                if (me == 1 || !kTwoIssuers) {
+                for (int j = 0; j < 4; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
 #pragma unroll
-                    for (int j = (kTwoIssuers ? 2 : 4); j < 4; ++j)
-                        mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, j > 2);
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dl + bo + j * kstep, ID, 1);
-                }
+                for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dl + bo + j * kstep, ID, 1);
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                             ::"r"(su32(&sy->mdone[b][me])) : "memory");
+                             ::"r"(su32(&sy->mdone[b])) : "memory");
             }
+            // the MMAs issued so far finish before the tensor memory is freed
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                         ::"r"(su32(&sy->drain)) : "memory");
+            mbar_wait_bounded(&sy->drain, 0);
         }
         __syncwarp();
     } else {
@@ -353,10 +384,12 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         float acc[NH];
 #pragma unroll
         for (int c = 0; c < NH; ++c) acc[c] = 0.f;
+        int q = 0;                               // ring buffer of stage st
+        uint32_t ph = 0;                         // its phase: (st / S) & 1
         for (int st = 0; st <= nstage && ok; ++st) {
             if (st < nstage) {
-                const int q = st % S, b = st & 1;
-                ok = mbar_wait_abort(&sy->full[q], uint32_t(st / S) & 1, abort);
+                const int b = st & 1;
+                ok = mbar_wait_abort(&sy->full[q], ph, abort);
                 if (!ok) break;
                 const unsigned char *sq = sS + q * rowb;
                 // B, high and low parts, in the canonical layout: piece p (grid
@@ -369,8 +402,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                     const float4 v = *reinterpret_cast<const float4 *>(sq + (nslot + c) * kSlotBytes + p * 16);
                     const int o = b * BB + (p * NB + c / 8) * 128 + (c % 8) * 16;
                     *reinterpret_cast<float4 *>(sHi + o) = v;
-                    *reinterpret_cast<float4 *>(sLo + o) =
-                        make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+                    uint4 l;
+                    lo2(v.x, v.y, l.x, l.y);
+                    lo2(v.z, v.w, l.z, l.w);
+                    *reinterpret_cast<uint4 *>(sLo + o) = l;
                 }
                 const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
                 const uint32_t a = tlane + 64 * b;
@@ -381,6 +416,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 default: form_a<false, true, true>(u8, v8, a, half); break;
                 }
                 mbar_arrive(&sy->empty[q]);
+                if (++q == S) { q = 0; ph ^= 1u; }
                 asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
@@ -390,12 +426,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 // accumulators of stage st - 1 (buffer b)
                 const int b = (st - 1) & 1;
                 const uint32_t par = uint32_t((st - 1) >> 1) & 1;
-                ok = mbar_wait_abort(&sy->mdone[b][0], par, abort) &&
-                     (!kTwoIssuers || mbar_wait_abort(&sy->mdone[b][1], par, abort));
+                ok = mbar_wait_abort(&sy->mdone[b], par, abort);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 add_accumulator<NH>(tlane + 128 + 64 * b + NH * half, acc);
-                if (kTwoIssuers) add_accumulator<NH>(tlane + 128 + 64 * b + 32 + NH * half, acc);
                 asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
                 mbar_arrive(&sy->dfree[b]);
             }
@@ -429,12 +463,13 @@ cudaError_t launch_class(const TcArgs &a, const float2 *dstore, int64_t u0, int6
 
 }  // namespace
 
-cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *cb, int nf, cudaStream_t s)
+cudaError_t launch_step2_tc(const TcArgs &a, const float2 *dstore, const int64_t *lo, const int64_t *hi, int nf,
+                            cudaStream_t s)
 {
-    cudaError_t e = launch_class<16>(a, dstore, cb[0], cb[1] - cb[0], nf, s);
-    if (e == cudaSuccess) e = launch_class<32>(a, dstore, cb[1], cb[2] - cb[1], nf, s);
-    if (e == cudaSuccess) e = launch_class<48>(a, dstore, cb[2], cb[3] - cb[2], nf, s);
-    if (e == cudaSuccess) e = launch_class<64>(a, dstore, cb[3], cb[4] - cb[3], nf, s);
+    cudaError_t e = launch_class<16>(a, dstore, lo[0], hi[0] - lo[0], nf, s);
+    if (e == cudaSuccess) e = launch_class<32>(a, dstore, lo[1], hi[1] - lo[1], nf, s);
+    if (e == cudaSuccess) e = launch_class<48>(a, dstore, lo[2], hi[2] - lo[2], nf, s);
+    if (e == cudaSuccess) e = launch_class<64>(a, dstore, lo[3], hi[3] - lo[3], nf, s);
     return e;
 }
 

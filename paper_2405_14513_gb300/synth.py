@@ -106,6 +106,16 @@ def default_k1_edges(ng: int, box_len: float, n_k1: int) -> np.ndarray:
     return e
 
 
+def log_k1_edges(ng: int, box_len: float, n_k1: int, lo: float | None = None) -> np.ndarray:
+    """k1 edges of equal logarithmic width (the paper's k1 binning) from `lo`
+    (default (N_g/12) k_f) to (N_g/3) k_f."""
+    kf = 2.0 * np.pi / box_len
+    hi = (ng / 3.0) * kf
+    e = np.geomspace(lo if lo is not None else (ng / 12.0) * kf, hi, n_k1 + 1)
+    e[-1] = hi
+    return e
+
+
 # ---------------------------------------------------------------------------
 # The same recipe with torch (for large grids on a GPU): the noise stream is
 # bit-identical to white_noise(); the transforms run in float64 with torch.fft.

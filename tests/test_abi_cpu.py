@@ -50,6 +50,9 @@ def test_status_strings():
     (dict(box_len=float("nan")), 1),
     (dict(edges="beyond"), 1),
     (dict(edges="descending"), 1),
+    (dict(n_mu_l=[12, 12, 8, 6]), 1),                         # per-l mu bins without t bins
+    (dict(n_mu_l=[12, 12, 8, 0], n_t_l=[12, 12, 8, 6]), 1),   # an empty grid
+    (dict(n_mu_l=[12, 12, 8, 6], n_t_l=[12, 12, 8, 5000]), 1),
 ])
 def test_plan_rejects_bad_arguments(kw, code):
     ng = kw.get("n_g", 32)
@@ -61,7 +64,7 @@ def test_plan_rejects_bad_arguments(kw, code):
     elif kw.get("edges") == "descending":
         e = e[::-1].copy()
     st, msg = api.try_plan(ng, L, e, kw.get("n_mu", 4), kw.get("n_t", 4), kw.get("l_max", 6),
-                           kw.get("precision", "mixed"), kw.get("max_batch", 1))
+                           kw.get("precision", "mixed"), kw.get("max_batch", 1), kw.get("n_mu_l"), kw.get("n_t_l"))
     assert st == code, msg
     assert msg
 

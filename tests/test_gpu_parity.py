@@ -356,3 +356,100 @@ def test_transform_tiles_do_not_change_results():
         outs.append(plan.estimate(f, plan.workspace(1)).cpu().numpy())
         plan.close()
     assert np.array_equal(outs[0], outs[1], equal_nan=True)
+
+
+# --------------------------------------------------------------------------
+# One estimate split into shares (estimator_estimate_part)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["mixed_tc", "mixed", "fp64"])
+def test_shares_sum_to_whole_estimate(precision):
+    """The Step-II work of an estimate split into nparts shares: the shares'
+    outputs add up to the whole estimate to FP64 rounding, for every field of
+    a batch, whatever ran in the workspace before (each share clears the
+    other shares' partial sums)."""
+    ng, L = 64, 1000.0
+    edges = synth.default_k1_edges(ng, L, 6)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = api.Plan(ng, L, edges, 5, 5, 6, precision=precision, max_batch=2)
+    ws = plan.workspace(2)
+    fields = torch.stack([torch.from_numpy(synth.make_field(ng, L, s)) for s in (51, 52)]).to(dt).cuda()
+    whole = plan.estimate(fields, ws).cpu().numpy()
+    for nparts in (2, 3, 7, 50):
+        shares = [plan.estimate_part(fields, ws, p, nparts).cpu().numpy() for p in range(nparts)]
+        total = np.sum(shares, axis=0)
+        for i in range(2):
+            assert floored_rel_err(total[i], whole[i]).max() < 1e-12, (nparts, i)
+        if nparts == 2:
+            fin = np.isfinite(whole)
+            for s in shares:
+                assert np.abs(s[fin]).max() > 0 and np.abs(s[fin] - whole[fin]).max() > 0
+    assert np.array_equal(plan.estimate_part(fields, ws, 0, 1).cpu().numpy(), whole, equal_nan=True)
+    for part, nparts in ((3, 3), (-1, 2), (0, 0)):
+        with pytest.raises(api.BispError):
+            plan.estimate_part(fields, ws, part, nparts)
+    plan.close()
+
+
+# --------------------------------------------------------------------------
+# Per-l (mu, t) grids and logarithmic k1 bins
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["mixed_tc", "fp64"])
+def test_per_l_grids_and_log_k1_bins(precision):
+    """The paper's binning: k1 bins of equal logarithmic width and (mu, t) grids
+    of 12, 12, 8 and 6 bins per axis for l = 0, 2, 4, 6.  Each view's block
+    matches the oracle estimate on that view's grid, and equals bit for bit
+    the same moments of a plan that bins every l on that grid (Step II and
+    the combination order do not depend on the (mu, t) grid)."""
+    ng, L = 48, 500.0
+    edges = synth.log_k1_edges(ng, L, 4)
+    dt = np.float64 if precision == "fp64" else np.float32
+    field = synth.make_field(ng, L, 61).astype(dt)
+    plan = api.Plan(ng, L, edges, 1, 1, 6, precision=precision, mu_t_bins_l=[12, 12, 8, 6])
+    assert [(v["l_lo"], v["l_hi"], v["n_mu"], v["n_t"], v["n_lm"]) for v in plan.views] == \
+        [(0, 2, 12, 12, 4), (4, 4, 8, 8, 5), (6, 6, 6, 6, 7)]
+    assert plan.out_shape(1) == (1, plan.out_doubles)
+    assert plan.out_doubles == sum(v["n_bins"] * v["n_lm"] for v in plan.views)
+    d = torch.from_numpy(field).cuda()[None].contiguous()
+    blocks = plan.split(plan.estimate(d, plan.workspace(1)).cpu().numpy())
+    dens = plan.split(plan.denominator()[None])
+    for v, blk, den in zip(plan.views, blocks, dens):
+        lm = slice((v["l_lo"] // 2) ** 2, (v["l_lo"] // 2) ** 2 + v["n_lm"])
+        ref = O.estimate(field.astype(np.float64), L, edges, v["n_mu"], v["n_t"], 6)
+        want = O.select_even(ref["B"], 6)[..., lm]
+        assert floored_rel_err(blk[0], want).max() < TOL[precision], v
+        dref = O.select_even(ref["den"], 6)[..., lm]
+        assert np.abs(den[0] - dref).max() <= 1e-12 * np.abs(dref).max()
+        one = api.Plan(ng, L, edges, v["n_mu"], v["n_t"], 6, precision=precision)
+        same = one.estimate(d, one.workspace(1)).cpu().numpy()[0][..., lm]
+        assert np.array_equal(blk[0], same, equal_nan=True), v
+        one.close()
+    plan.close()
+
+
+# --------------------------------------------------------------------------
+# Statistics over many mocks (estimator_stats_update, mocks.run_mocks)
+# --------------------------------------------------------------------------
+def test_mock_statistics_match_per_field_estimates():
+    """Ten seeded mocks, four per captured launch (two graph replays and a
+    partial batch of two): the device-side running count, mean and standard
+    deviation of B equal those of the ten estimates made one by one."""
+    from paper_2405_14513_gb300 import mocks
+    ng, L = 32, 500.0
+    edges = synth.default_k1_edges(ng, L, 3)
+    plan = api.Plan(ng, L, edges, 4, 4, 6, precision="mixed_tc", max_batch=4)
+    seeds = list(range(100, 110))
+    c, mean, std = mocks.run_mocks(plan, seeds, 4).numpy()
+    ws = plan.workspace(1)
+    one = np.stack([plan.estimate(synth.make_field_torch(ng, L, s, device="cuda").float()[None].contiguous(),
+                                  ws).cpu().numpy()[0] for s in seeds])
+    fin = np.isfinite(one)
+    assert np.array_equal(c, fin.sum(axis=0))
+    ok = c > 1
+    assert ok.any()
+    scale = np.nanmax(np.abs(one))
+    ref_mean = np.nanmean(np.where(fin, one, np.nan), axis=0)
+    ref_std = np.nanstd(np.where(fin, one, np.nan), axis=0, ddof=1)
+    assert np.abs(mean[ok] - ref_mean[ok]).max() <= 1e-12 * scale
+    assert np.abs(std[ok] - ref_std[ok]).max() <= 1e-10 * scale
+    assert np.isnan(mean[c == 0]).all()
+    plan.close()
