@@ -279,8 +279,7 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
             CK(cudaMemcpyAsync(d_joff, joff.data(), joff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
             CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lv].size()), M, true, gt,
                                           p->tw_d, Batch{}, s));
-            CK(launch_fft_rows_T<double>(gt, I, M, M, int64_t(jobs[lv].size()), d_joff, 1.0, false, p->tw_d,
-                                         Batch{}, s));
+            CK(launch_fft_cols<double>(gt, I, M, int64_t(jobs[lv].size()), d_joff, p->tw_d, Batch{}, s));
             CK(cudaStreamSynchronize(s));   // the job tables are reused by the next grid
         }
         CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), p->grid_arg, d_raw, s));
@@ -320,14 +319,16 @@ int init_attributes()
     return BISP_OK;
 }
 
-// Transform tile autotuner.  Each transform kernel holds rt rows of its
-// length M in two shared-memory buffers; the best rt depends on M, the
-// kernel and the GPU (large tiles leave one block per SM).  For the forward
-// z pass, the forward row passes and each reduction grid's gather and row
-// pass, candidate tiles of 4-64 KB per buffer are timed on scratch buffers
-// holding a sample of the plan's rows (at most 64 fields of a grid, 16
-// planes, 64K z rows), and the fastest is kept.  Rows are transformed
-// independently, so the choice changes the speed, not the results.
+// Transform tile autotuner.  Each transform kernel holds rt rows (or, in
+// Step I's second pass, w columns) of its length M in two shared-memory
+// buffers; the best tile depends on M, the kernel and the GPU (large tiles
+// leave one block per SM).  For the forward z pass, the forward row passes
+// and each reduction grid's gather, candidate tiles of 4-64 KB per buffer,
+// and for each grid's second pass strips of 2-32 columns, are timed on
+// scratch buffers holding a sample of the plan's rows (at most 64 fields of
+// a grid, 16 planes, 64K z rows), and the fastest is kept.  Rows and
+// columns are transformed independently, so the choice changes the speed,
+// not the results.
 template <typename R>
 int autotune_transforms(bisp_plan *p, cudaStream_t s)
 {
@@ -360,8 +361,14 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     C *planes = static_cast<C *>(talloc(bplanes));
     C *b0 = static_cast<C *>(talloc(bout));
     C *b1 = static_cast<C *>(talloc(brows));
+    // output offsets of the sample jobs of every grid (job j at j M^2)
+    int64_t *d_offs = static_cast<int64_t *>(talloc(sizeof(int64_t) * 64 * P.levels.size()));
+    std::vector<int64_t> h_offs(64 * P.levels.size());
+    for (size_t l = 0; l < P.levels.size(); ++l)
+        for (int j = 0; j < 64; ++j) h_offs[64 * l + j] = int64_t(j) * P.levels[l].M * P.levels[l].M;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (!zin || !planes || !b0 || !b1 || cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (!zin || !planes || !b0 || !b1 || !d_offs || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
         if (e0) cudaEventDestroy(e0);
@@ -371,6 +378,7 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     cudaMemsetAsync(planes, 0, bplanes, s);
     cudaMemsetAsync(b0, 0, bout, s);
     cudaMemsetAsync(b1, 0, brows, s);
+    cudaMemcpyAsync(d_offs, h_offs.data(), h_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
     const size_t cand[] = {4096, 8192, 16384, 32768, 65536};
     // the fastest of the candidate rows per block for one launch
     auto pick = [&](int M, int cap, auto &&launch) -> int {
@@ -391,6 +399,23 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
         }
         return best;
     };
+    // the fastest strip width (columns per block) of a grid's second pass
+    auto pick_w = [&](int M, auto &&launch) -> int {
+        int best = 0;
+        float best_ms = 1e30f;
+        for (int w : {2, 4, 8, 16, 32}) {
+            if (w > M || size_t(2) * w * (M + 1) * sizeof(C) > 227 * 1024) continue;
+            if (launch(w) != cudaSuccess) return -1;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch(w);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return -1;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) { best_ms = ms; best = w; }
+        }
+        return best;
+    };
     const Batch one{};
     int st = BISP_OK;
     p->rt_z = pick(ng, 256, [&](int rt) {
@@ -403,11 +428,12 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     for (size_t l = 0; l < P.levels.size() && !st; ++l) {
         const Level &L = P.levels[l];
         const int64_t nj = std::min<int64_t>(L.njobs, 64);
+        const int64_t *d_off = d_offs + 64 * l;
         const int g = pick(L.M, L.M, [&](int rt) {
             return launch_ring_gather<R>(planes, ng, p->ring_arg, p->d_jobs[l], nj, L.M, false, b0, tw, one, s, rt);
         });
-        const int r = pick(L.M, L.M, [&](int rt) {
-            return launch_fft_rows_T<R>(b0, b1, L.M, L.M, nj, nullptr, R(1), false, tw, one, s, rt);
+        const int r = pick_w(L.M, [&](int w) {
+            return launch_fft_cols<R>(b0, b1, L.M, nj, d_off, tw, one, s, w);
         });
         if (g < 0 || r < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
         p->rt_gather[L.lev] = std::max(g, 0);
@@ -449,8 +475,9 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     for (int r = 0; r < R.nr; ++r) p->ring_arg.maxc[r] = R.maxc[r];
 
     for (int l = 0; l < R.ngrid; ++l) p->grid_arg.M[l] = R.grid[l];
-    // twiddles in double: exp(-2 pi i k / N_g), k < N_g / 2, for the lengths
-    // 2^q, and exp(-2 pi i k / (3 N_g / 2)), k < 3 N_g / 4, for 3 x 2^q
+    // twiddles in double: exp(-2 pi i k / 2^lg2), k < 3/4 of 2^lg2, for the
+    // lengths 2^q, and exp(-2 pi i k / (3 x 2^lg3)), k < 3/4 of 3 x 2^lg3, for
+    // 3 x 2^q (three quarters of the circle: radix-4 stages reach it)
     {
         // lengths 2^q <= N_g use exp(-2 pi i k / 2^lg2); lengths 3 x 2^q <= N_g
         // use exp(-2 pi i k / (3 x 2^lg3))
@@ -472,8 +499,8 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
         };
         float2 *f2 = nullptr, *f3 = nullptr;
         double2 *d2 = nullptr, *d3 = nullptr;
-        int st = table(1 << lg2, 1 << (lg2 - 1), &f2, &d2);
-        if (!st) st = table(3 << lg3, 3 << (lg3 - 1), &f3, &d3);
+        int st = table(1 << lg2, (3 * (1 << lg2) + 3) / 4, &f2, &d2);
+        if (!st) st = table(3 << lg3, (3 * (3 << lg3) + 3) / 4, &f3, &d3);
         if (st) return st;
         p->tw_f = Twiddles<float2>{f2, f3, lg2, lg3};
         p->tw_d = Twiddles<double2>{d2, d3, lg2, lg3};
@@ -621,8 +648,7 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
             const int M = L.M;
             CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, region, s,
                                      p->rt_gather[L.lev]));
-            CK(launch_fft_rows_T<R>(gt, dstore, M, M, L.njobs, p->d_job_off[l], R(1), false, tw, region, s,
-                                    p->rt_rows[L.lev]));
+            CK(launch_fft_cols<R>(gt, dstore, M, L.njobs, p->d_job_off[l], tw, region, s, p->rt_rows[L.lev]));
         }
     }
     {   // Step II: triple sums (Eq. fftbs), all units or one share of them

@@ -53,23 +53,49 @@ template <typename T> __device__ __forceinline__ const T *field_ptr(const T *p, 
     return reinterpret_cast<const T *>(reinterpret_cast<const char *>(p) + int64_t(blockIdx.y) * fs);
 }
 
+// t = q d + r along t = t0, t0 + step, ...: quotient and remainder kept
+// incrementally (one division per thread rather than one per element)
+struct DivIter {
+    int q, r, dq, dr, d;
+    __device__ __forceinline__ DivIter(int t0, int step, int d_) : d(d_)
+    {
+        q = t0 / d;
+        r = t0 - q * d;
+        dq = step / d;
+        dr = step - dq * d;
+    }
+    __device__ __forceinline__ void next()
+    {
+        q += dq;
+        r += dr;
+        if (r >= d) {
+            r -= d;
+            ++q;
+        }
+    }
+};
+
 // Stockham transform of nrows rows of length M = 2^q or 3 x 2^q held in
 // shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M): one
-// radix-3 stage first when 3 divides M, then radix-2 stages.  Every thread
+// radix-3 stage first when 3 divides M, then radix-4 stages and, for an odd
+// power of two, one radix-2 stage.  Every thread
 // of the block takes part; the caller synchronises before the call.  The
 // result is in the returned buffer (a or b).
 template <typename C>
 __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
 {
     using Rr = decltype(a[0].x);
-    const bool has3 = (M % 3) == 0;
+    // M = 2^p or 3 x 2^p: every index split below is a shift, or a shift and
+    // a division by the constant 3
+    const int p = __ffs(M) - 1;
+    const bool has3 = (M >> p) == 3;
     int Ns = 1;
     if (has3) {
         const int third = M / 3;
         const int total = nrows * third;
         const Rr h = Rr(0.86602540378443864676);   // sqrt(3)/2
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int row = t / third, j = t - row * third;
+            const int row = t >> p, j = t & (third - 1);
             const C v0 = a[row * P + j], v1 = a[row * P + j + third], v2 = a[row * P + j + 2 * third];
             const Rr sx = v1.x + v2.x, sy = v1.y + v2.y, dx = v1.x - v2.x, dy = v1.y - v2.y;
             const Rr mx = v0.x - Rr(0.5) * sx, my = v0.y - Rr(0.5) * sy;
@@ -87,20 +113,56 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
         b = t2;
         Ns = 3;
     }
-    const int half = M / 2;
-    const int total = nrows * half;
-    for (int s = 0; Ns < M; ++s, Ns *= 2) {
-        // twiddle exp(-2 pi i k / (2 Ns)) from the table of the matching family
-        const C *wt = has3 ? tw.tw3 : tw.tw2;
-        const int sh = (has3 ? tw.lg3 : tw.lg2) - s - 1;
-        for (int t = threadIdx.x; t < total; t += blockDim.x) {
-            const int row = t / half, j = t - row * half;
-            const int q = j / Ns, k = j - q * Ns;
-            C v0 = a[row * P + j];
-            C v1 = cmul(a[row * P + j + half], __ldg(&wt[k << sh]));
-            const int idx = q * 2 * Ns + k;
-            b[row * P + idx] = cadd(v0, v1);
-            b[row * P + idx + Ns] = csub(v0, v1);
+    const C *wt = has3 ? tw.tw3 : tw.tw2;
+    const int lg = has3 ? tw.lg3 : tw.lg2;
+    int s = 0;                                  // Ns = 2^s (times 3 if has3)
+    while (Ns < M) {
+        if (M / Ns >= 4) {
+            // radix 4: v_r = x[j + r M/4] w^(rk), w = exp(-2 pi i / (4 Ns)),
+            // out[q 4 Ns + k + m Ns] = sum_r v_r (-i)^(rm)
+            const int quarter = M / 4;
+            const int total = nrows * quarter;
+            const int sh = lg - s - 2;
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                const int row = has3 ? int(unsigned(t >> (p - 2)) / 3u) : (t >> (p - 2));
+                const int j = t - row * quarter;
+                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int k = j - q * Ns;
+                const C *src = a + row * P + j;
+                const C v0 = src[0];
+                const C v1 = cmul(src[quarter], __ldg(&wt[k << sh]));
+                const C v2 = cmul(src[2 * quarter], __ldg(&wt[(2 * k) << sh]));
+                const C v3 = cmul(src[3 * quarter], __ldg(&wt[(3 * k) << sh]));
+                const C s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
+                C *dst = b + row * P + q * 4 * Ns + k;
+                dst[0] = cadd(s02, s13);
+                dst[2 * Ns] = csub(s02, s13);
+                // -i d13 = (d13.y, -d13.x)
+                C m1 = d02, m3 = d02;
+                m1.x += d13.y; m1.y -= d13.x;
+                m3.x -= d13.y; m3.y += d13.x;
+                dst[Ns] = m1;
+                dst[3 * Ns] = m3;
+            }
+            Ns *= 4;
+            s += 2;
+        } else {
+            const int half = M / 2;
+            const int total = nrows * half;
+            const int sh = lg - s - 1;
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                const int row = has3 ? int(unsigned(t >> (p - 1)) / 3u) : (t >> (p - 1));
+                const int j = t - row * half;
+                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int k = j - q * Ns;
+                C v0 = a[row * P + j];
+                C v1 = cmul(a[row * P + j + half], __ldg(&wt[k << sh]));
+                const int idx = q * 2 * Ns + k;
+                b[row * P + idx] = cadd(v0, v1);
+                b[row * P + idx + Ns] = csub(v0, v1);
+            }
+            Ns *= 2;
+            s += 1;
         }
         __syncthreads();
         C *t2 = a;
@@ -125,14 +187,16 @@ k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int 
     C *b = a + rt * P;
     const int64_t row0 = int64_t(blockIdx.x) * rt;
     const int nrow = int(min(int64_t(rt), rows - row0));
-    for (int t = threadIdx.x; t < nrow * M; t += blockDim.x) {
-        const int r = t / M, j = t - r * M;
+    DivIter ld(threadIdx.x, blockDim.x, M);
+    for (int t = threadIdx.x; t < nrow * M; t += blockDim.x, ld.next()) {
+        const int r = ld.q, j = ld.r;
         a[r * P + j] = cmk<C>(double(in[(row0 + r) * M + j]), 0.0);
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nrow, tw);
-    for (int t = threadIdx.x; t < nkeep * nrow; t += blockDim.x) {
-        const int k = t / nrow, r = t - k * nrow;
+    DivIter st(threadIdx.x, blockDim.x, nrow);
+    for (int t = threadIdx.x; t < nkeep * nrow; t += blockDim.x, st.next()) {
+        const int k = st.q, r = st.r;
         out[int64_t(k) * rows + row0 + r] = res[r * P + k];
     }
 }
@@ -155,15 +219,17 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
     const int row0 = tile * rt;
     const int nr = min(rt, nrow - row0);
     const C *src = in + bt * int64_t(M) * nrow;
-    for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
-        const int r = t / M, j = t - r * M;
+    DivIter ld(threadIdx.x, blockDim.x, M);
+    for (int t = threadIdx.x; t < nr * M; t += blockDim.x, ld.next()) {
+        const int r = ld.q, j = ld.r;
         a[r * P + j] = src[int64_t(row0 + r) * M + j];
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nr, tw);
     C *dst = out + (out_off ? out_off[bt] : bt * int64_t(M) * nrow);
-    for (int t = threadIdx.x; t < M * nr; t += blockDim.x) {
-        const int k = t / nr, r = t - k * nr;
+    DivIter st(threadIdx.x, blockDim.x, nr);
+    for (int t = threadIdx.x; t < M * nr; t += blockDim.x, st.next()) {
+        const int k = st.q, r = st.r;
         C v = res[r * P + k];
         v.x *= scale;
         v.y *= scale;
@@ -193,8 +259,9 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     const int mc = rings.maxc[J.r];
     const int row0 = tile * rt;
     const int nr = min(rt, M - row0);
-    for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
-        const int tr = t / M, j = t - tr * M;
+    DivIter ld(threadIdx.x, blockDim.x, M);
+    for (int t = threadIdx.x; t < nr * M; t += blockDim.x, ld.next()) {
+        const int tr = ld.q, j = ld.r;
         const int i = row0 + tr;
         R vr = 0, vi = 0;
         // members u with u_x = i or i - M and u_y = j or j - M (mod M folding;
@@ -222,10 +289,47 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nr, tw);
-    C *dst = gt + jb * int64_t(M) * M;
-    for (int t = threadIdx.x; t < M * nr; t += blockDim.x) {
-        const int k = t / nr, r = t - k * nr;
-        dst[int64_t(k) * M + row0 + r] = res[r * P + k];
+    // rows of the job's M x M field in place (u_x, k_y), whole rows: coalesced
+    C *dst = gt + jb * int64_t(M) * M + int64_t(row0) * M;
+    DivIter st(threadIdx.x, blockDim.x, M);
+    for (int t = threadIdx.x; t < M * nr; t += blockDim.x, st.next()) {
+        const int r = st.q, k = st.r;
+        dst[t] = res[r * P + k];
+    }
+}
+
+// Step I second pass: transforms along the first axis of each job's M x M
+// field (rows u_x of the gather's output), a strip of w columns k_y per
+// block, read and written in place order (runs of w consecutive elements
+// of every row), so the D field comes out as [k_x][k_y].
+template <typename R>
+__global__ void __launch_bounds__(256)
+k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M, int ntile, int w,
+           const int64_t *__restrict__ out_off, Twiddles<typename Cx<R>::T> tw, int64_t fs)
+{
+    using C = typename Cx<R>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    in = field_ptr(in, fs);
+    out = field_ptr(out, fs);
+    const int P = M + 1;
+    C *a = reinterpret_cast<C *>(smem_raw);
+    C *b = a + w * P;
+    const int64_t jb = blockIdx.x / ntile;
+    const int c0 = int(blockIdx.x - jb * ntile) * w;
+    const int nc = min(w, M - c0);
+    const C *src = in + jb * int64_t(M) * M + c0;
+    DivIter ld(threadIdx.x, blockDim.x, nc);
+    for (int t = threadIdx.x; t < M * nc; t += blockDim.x, ld.next()) {
+        const int i = ld.q, c = ld.r;
+        a[c * P + i] = src[int64_t(i) * M + c];
+    }
+    __syncthreads();
+    const C *res = fft_smem(a, b, M, P, nc, tw);
+    C *dst = out + out_off[jb] + c0;
+    DivIter st(threadIdx.x, blockDim.x, nc);
+    for (int t = threadIdx.x; t < M * nc; t += blockDim.x, st.next()) {
+        const int k = st.q, c = st.r;
+        dst[int64_t(k) * M + c] = res[c * P + k];
     }
 }
 
@@ -594,6 +698,23 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int64_t njobs,
+                            const int64_t *out_off, const Twiddles<typename Cx<R>::T> &tw, const Batch &fb,
+                            cudaStream_t s, int w)
+{
+    using C = typename Cx<R>::T;
+    if (w <= 0) w = 8;
+    w = std::min(w, M);
+    const size_t smem = size_t(2) * w * (M + 1) * sizeof(C);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    const int ntile = (M + w - 1) / w;
+    const int64_t nblk = njobs * ntile;
+    if (nblk == 0) return cudaSuccess;
+    k_fft_cols<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, M, ntile, w, out_off, tw, fb.fs_in);
+    return cudaGetLastError();
+}
+
 template <typename R, int NW>
 cudaError_t launch_step2_class(const StepIIArgs &a, const typename Cx<R>::T *dstore, int64_t u0, int64_t n,
                                size_t smem, int nf, cudaStream_t s)
@@ -677,6 +798,8 @@ cudaError_t init_kernel_attributes()
     set((const void *)k_fft_z_real<double>);
     set((const void *)k_fft_rows_T<float>);
     set((const void *)k_fft_rows_T<double>);
+    set((const void *)k_fft_cols<float>);
+    set((const void *)k_fft_cols<double>);
     set((const void *)k_ring_gather<float, false>);
     set((const void *)k_ring_gather<float, true>);
     set((const void *)k_ring_gather<double, false>);
@@ -727,6 +850,10 @@ template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int
 template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
+template cudaError_t launch_fft_cols<float>(const float2 *, float2 *, int, int64_t, const int64_t *, const Twiddles<float2> &,
+                                            const Batch &, cudaStream_t, int);
+template cudaError_t launch_fft_cols<double>(const double2 *, double2 *, int, int64_t, const int64_t *,
+                                             const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, const int64_t *, int,
                                          cudaStream_t);
 template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, const int64_t *, const int64_t *, int,

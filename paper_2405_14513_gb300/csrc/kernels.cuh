@@ -79,13 +79,22 @@ cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *ou
                               int rt = 0);
 
 // Step I, first pass: ring r of plane n of Delta (planes [nz+1][ng][ng]),
-// folded onto the M x M grid, transformed along u_y, written transposed to
-// gt[job][y_y][i].  unit = true uses Delta = 1 (the unit fields of Eq. 2FT).
+// folded onto the M x M grid, transformed along u_y, written in place order
+// to gt[job][u_x][k_y].  unit = true uses Delta = 1 (the unit fields of
+// Eq. 2FT).
 template <typename R>
 cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const RingArg &rings,
                                const Job *jobs, int64_t njobs, int M, bool unit,
                                typename Cx<R>::T *gt, const Twiddles<typename Cx<R>::T> &tw,
                                const Batch &fb, cudaStream_t s, int rt = 0);
+
+// Step I second pass: for each of njobs M x M fields in gt ([u_x][k_y],
+// the gather's output), transforms along u_x in strips of w columns and
+// writes the field [k_x][k_y] at out + out_off[job].
+template <typename R>
+cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int64_t njobs,
+                            const int64_t *out_off, const Twiddles<typename Cx<R>::T> &tw, const Batch &fb,
+                            cudaStream_t s, int w = 0);
 
 // Step II: partial triple sums of units, one block per unit, one launch per
 // block class (units [lo[c], hi[c]) run in blocks of 2^c warps with
