@@ -91,11 +91,14 @@ __device__ __forceinline__ void lo2(float x, float y, uint32_t &lx, uint32_t &ly
     ly = __float_as_uint(b);
 }
 
+// No memory clobber: tensor memory is not memory the compiler tracks, so
+// shared-memory loads of the next points may be scheduled across the store
+// (its order against tcgen05.wait::st and the fences, all volatile, stays).
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8])
 {
     asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n"
                  ::"r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]),
-                   "r"(v[7]) : "memory");
+                   "r"(v[7]));
 }
 
 // The loads below keep the wait in the same statement, so the registers are
@@ -392,6 +395,14 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 ok = mbar_wait_abort(&sy->full[q], ph, abort);
                 if (!ok) break;
                 const unsigned char *sq = sS + q * rowb;
+                const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
+                const uint32_t a = tlane + 64 * b;
+                switch (T.flags) {   // uniform over the tile; n1 >= 0 (half space)
+                case 0: form_a<false, false, false>(u8, v8, a, half); break;
+                case 2: form_a<false, true, false>(u8, v8, a, half); break;
+                case 4: form_a<false, false, true>(u8, v8, a, half); break;
+                default: form_a<false, true, true>(u8, v8, a, half); break;
+                }
                 // B, high and low parts, in the canonical layout: piece p (grid
                 // points 2p, 2p + 1) of column c goes to core matrix (K block p,
                 // rows 8 (c / 8) ..), row c % 8.  Buffer b was last read by the
@@ -406,14 +417,6 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                     lo2(v.x, v.y, l.x, l.y);
                     lo2(v.z, v.w, l.z, l.w);
                     *reinterpret_cast<uint4 *>(sLo + o) = l;
-                }
-                const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
-                const uint32_t a = tlane + 64 * b;
-                switch (T.flags) {   // uniform over the tile; n1 >= 0 (half space)
-                case 0: form_a<false, false, false>(u8, v8, a, half); break;
-                case 2: form_a<false, true, false>(u8, v8, a, half); break;
-                case 4: form_a<false, false, true>(u8, v8, a, half); break;
-                default: form_a<false, true, true>(u8, v8, a, half); break;
                 }
                 mbar_arrive(&sy->empty[q]);
                 if (++q == S) { q = 0; ph ^= 1u; }
