@@ -242,6 +242,54 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
             if (slot_of(cur.slots, k.second) < 0) cur.slots.push_back(k.second);
         }
         if (int(cur.slots.size()) != T.nslot) return "tcgen05 tile slots";
+        // Bank groups: a 16-byte load of slot s falls in bank group s % 8
+        // (slot stride 144 bytes), and the 8 lanes of a load phase that read
+        // different slots of one group are served one after another.  Colour
+        // the fields greedily (first appearance order) so that the distinct
+        // D1 fields of each 8-row phase, and its distinct D2 fields, take
+        // distinct colours where they can, and number them colour + 8 k;
+        // numbers left free are padding slots that hold a field nothing
+        // stores (they read as zero).  Kept only if the tile still fits.
+        const int ns = T.nslot;
+        std::vector<int> num(ns);
+        {
+            std::vector<std::vector<int>> adj(ns);
+            for (size_t g0 = 0; g0 < cur.rows.size(); g0 += 8) {
+                std::vector<int> U, V;
+                for (size_t r = g0; r < std::min(cur.rows.size(), g0 + 8); ++r) {
+                    const auto k = keys(cur.rows[r]);
+                    const int f1 = slot_of(cur.slots, k.first), f2 = slot_of(cur.slots, k.second);
+                    if (std::find(U.begin(), U.end(), f1) == U.end()) U.push_back(f1);
+                    if (std::find(V.begin(), V.end(), f2) == V.end()) V.push_back(f2);
+                }
+                for (const auto *grp : {&U, &V})
+                    for (int a : *grp)
+                        for (int b : *grp)
+                            if (a != b) adj[a].push_back(b);
+            }
+            std::vector<int> col(ns, -1), cnt(8, 0), next(8, 0);
+            int top = 0;
+            for (int f = 0; f < ns; ++f) {
+                int use[8] = {0};
+                for (int n : adj[f])
+                    if (col[n] >= 0) ++use[col[n]];
+                int best = 0;
+                for (int c = 1; c < 8; ++c)
+                    if (use[c] < use[best] || (use[c] == use[best] && cnt[c] < cnt[best])) best = c;
+                col[f] = best;
+                ++cnt[best];
+                num[f] = best + 8 * next[best]++;
+                top = std::max(top, num[f] + 1);
+            }
+            if (top <= kTcMaxSlots && tc_stages(T.ncol, top) > 0) {
+                std::vector<int32_t> sl(size_t(top), (0 << 8) | R.nr);   // ring nr: never stored
+                for (int f = 0; f < ns; ++f) sl[num[f]] = cur.slots[f];
+                cur.slots.swap(sl);
+                T.nslot = top;
+            } else {
+                for (int f = 0; f < ns; ++f) num[f] = f;
+            }
+        }
         for (auto &gr : cur.rows) {
             const Group &G = P.groups[gr.first];
             const Row &rw = P.rows[gr.second];
@@ -249,8 +297,9 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
             t.p0 = G.part0 + rw.coff;
             t.stride = G.ncombo;
             const int a1 = G.n1 < 0 ? -G.n1 : G.n1, a2 = G.n2 < 0 ? -G.n2 : G.n2;
-            t.s1 = uint8_t(slot_of(cur.slots, (a1 << 8) | rw.r1));
-            t.s2 = uint8_t(slot_of(cur.slots, (a2 << 8) | rw.r2));
+            const auto k = keys(gr);
+            t.s1 = uint8_t(slot_of(cur.slots, k.first));     // the field's number (its slot)
+            t.s2 = uint8_t(slot_of(cur.slots, k.second));
             t.col0 = uint8_t(rw.r3a - cur.lo);
             t.n = rw.n;
             t.flags = uint8_t((G.n1 < 0 ? 1 : 0) | (G.n2 < 0 ? 2 : 0) | (G.n3 < 0 ? 4 : 0));
