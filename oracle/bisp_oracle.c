@@ -1086,3 +1086,234 @@ void bo_orientation(double mu1, double mu2, double mu, double *pz, double *px)
 {
     orient_inverse(mu1, mu2, mu, pz, px);
 }
+
+/* ======================================================================== */
+/* Spherical-shell estimator of the m = 0 multipoles.                       */
+/*                                                                          */
+/* The FFT estimators the paper builds on (Sec. I) bin k in spherical        */
+/* shells; with the weight of each mode's own direction they reach the m = 0 */
+/* moments only.  Written out here as a comparison for that subset:          */
+/*   shells     s = {k : e_s <= |k| < e_{s+1}} with |k| the 3D length and the */
+/*              ring edges e (the same width rule); shell 0 = {0} is unused;  */
+/*              K_s = mean |k| over the shell                                */
+/*   triples    s1 >= s2 >= s3 >= 1 (then K1 >= K2 >= K3), binned in          */
+/*              (k1, mu, t) from (K1, K2, K3) like a combination with n = 0;  */
+/*              kept when N_tri > 0                                          */
+/*   sums       over closed triangles k1 + k2 + k3 = 0, k_i in s_i:           */
+/*                num_l = sum Y_l0(k1) Delta(k1) Delta(k2) Delta(k3)          */
+/*                den_l = sum Y_l0(k1)^2,   N_tri = sum 1                     */
+/*              Y_l0(k) = sqrt((2l+1)/4pi) P_l(k_z / |k|); even l            */
+/*   FFT form   num_l = N^-3 sum_x F_{s1,l} D_{s2} D_{s3}, with               */
+/*              F_{s,l}(x) = sum_{k in s} Y_l0(k) Delta(k) e^{-ik.x},         */
+/*              D_s the same without Y; den_l and N_tri alike from            */
+/*              sum_{k in s} Y_l0^2 e^{-ik.x} and sum_{k in s} e^{-ik.x}      */
+/*   result     B_l^0 = sqrt((2l+1)/4pi) sum Re num_l / (V sum den_l) over    */
+/*              the bin's triples; NaN where sum den_l = 0                   */
+/* mode 0: FFT form; 1: the direct sums over mode pairs.                    */
+/* ======================================================================== */
+typedef struct {
+    int ng, ns;
+    long e3[BO_MAX_RINGS + 1];
+    double K[BO_MAX_RINGS];
+    int *idx;          /* shell of cube point (FFT index order, kz fastest), -1 outside */
+} shells_t;
+
+static int shells_build(int ng, shells_t *S)
+{
+    S->ng = ng;
+    S->ns = ring_edges3(ng, S->e3);
+    if (S->ns < 0) return -1;
+    long n3 = (long)ng * ng * ng;
+    S->idx = malloc(sizeof(int) * (size_t)n3);
+    double sum[BO_MAX_RINGS];
+    long cnt[BO_MAX_RINGS];
+    for (int s = 0; s < S->ns; ++s) { sum[s] = 0; cnt[s] = 0; }
+    for (long a = 0; a < ng; ++a)
+        for (long b = 0; b < ng; ++b)
+            for (long c = 0; c < ng; ++c) {
+                long i = signed_freq(a, ng), j = signed_freq(b, ng), n = signed_freq(c, ng);
+                long q9 = 9 * (i * i + j * j + n * n);
+                int sh = -1;
+                for (int s = 0; s < S->ns; ++s)
+                    if (S->e3[s] * S->e3[s] <= q9 && q9 < S->e3[s + 1] * S->e3[s + 1]) { sh = s; break; }
+                S->idx[(a * ng + b) * ng + c] = sh;
+                if (sh >= 0) { sum[sh] += sqrt((double)(i * i + j * j + n * n)); cnt[sh] += 1; }
+            }
+    for (int s = 0; s < S->ns; ++s) S->K[s] = cnt[s] > 0 ? sum[s] / (double)cnt[s] : 0.0;
+    return 0;
+}
+
+static double legendre_even(int l, double z)
+{
+    return assoc_legendre(l, 0, z);
+}
+
+/* Y_l0 of the direction of cube point (a, b, c) (k != 0) */
+static double y_l0_at(int l, int ng, long a, long b, long c)
+{
+    long i = signed_freq(a, ng), j = signed_freq(b, ng), n = signed_freq(c, ng);
+    double k = sqrt((double)(i * i + j * j + n * n));
+    return ylm_norm(l, 0) * legendre_even(l, (double)n / k);
+}
+
+/* field sum_{k in s} w(k) e^{-ik.x} on the cube, w = value * Y_l0^power */
+static void shell_field(const shells_t *S, const cplx *cube, int s, int l, int power, cplx *out)
+{
+    int ng = S->ng;
+    long n3 = (long)ng * ng * ng;
+    for (long p = 0; p < n3; ++p) {
+        if (S->idx[p] != s) { out[p] = 0; continue; }
+        long a = p / ((long)ng * ng), b = (p / ng) % ng, c = p % ng;
+        double w = 1.0;
+        for (int q = 0; q < power; ++q) w *= y_l0_at(l, ng, a, b, c);
+        out[p] = (cube ? cube[p] : 1.0) * w;
+    }
+    dft3(out, ng);
+}
+
+/* Accepted triples and their sums.  tri[k][4] = s1, s2, s3, bin; ntri[k];
+ * num/den [k][nl] (nl = l_max/2 + 1, l = 0, 2, ..).  delta may be NULL
+ * (num left 0).  Returns the count (all of it, even beyond cap), or -1. */
+long bo_shell_triples(const bo_desc *d, const double *delta, long cap, int *tri, double *ntri,
+                      double *num, double *den)
+{
+    if (desc_check(d) || (d->l_max & 1)) return -1;
+    set_threads(d->nthreads);
+    shells_t S;
+    if (shells_build(d->ng, &S)) return -1;
+    int ng = d->ng, ns = S.ns, nl = d->l_max / 2 + 1;
+    long n3 = (long)ng * ng * ng;
+    cplx *cube = delta ? forward_cube(ng, d->box_len, delta) : NULL;
+    long n = 0;
+    if (d->mode == 0) {
+        /* fields: D_s, F_{s,l} (l >= 2), I_s, G_{s,l} */
+        cplx **D = calloc((size_t)ns, sizeof(cplx *)), **I1 = calloc((size_t)ns, sizeof(cplx *));
+        cplx **F = calloc((size_t)ns * nl, sizeof(cplx *)), **G = calloc((size_t)ns * nl, sizeof(cplx *));
+        for (int s = 1; s < ns; ++s) {
+            I1[s] = malloc(sizeof(cplx) * (size_t)n3);
+            shell_field(&S, NULL, s, 0, 0, I1[s]);
+            for (int li = 0; li < nl; ++li) {
+                G[s * nl + li] = malloc(sizeof(cplx) * (size_t)n3);
+                shell_field(&S, NULL, s, 2 * li, 2, G[s * nl + li]);
+            }
+            if (cube) {
+                D[s] = malloc(sizeof(cplx) * (size_t)n3);
+                shell_field(&S, cube, s, 0, 0, D[s]);
+                for (int li = 0; li < nl; ++li) {
+                    F[s * nl + li] = malloc(sizeof(cplx) * (size_t)n3);
+                    shell_field(&S, cube, s, 2 * li, 1, F[s * nl + li]);
+                }
+            }
+        }
+        for (int s1 = 1; s1 < ns; ++s1)
+            for (int s2 = 1; s2 <= s1; ++s2)
+                for (int s3 = 1; s3 <= s2; ++s3) {
+                    geom_t g;
+                    if (!combo_geometry(d, S.K[s1], S.K[s2], S.K[s3], 0, 0, 0, &g)) continue;
+                    cplx t = 0;
+                    for (long p = 0; p < n3; ++p) t += I1[s1][p] * I1[s2][p] * I1[s3][p];
+                    double cnt = creal(t) / (double)n3;
+                    if (!(cnt > 0.5)) continue;
+                    if (n < cap) {
+                        tri[4 * n] = s1; tri[4 * n + 1] = s2; tri[4 * n + 2] = s3; tri[4 * n + 3] = g.bin;
+                        ntri[n] = floor(cnt + 0.5);
+                        for (int li = 0; li < nl; ++li) {
+                            cplx u = 0, v = 0;
+                            for (long p = 0; p < n3; ++p) {
+                                u += G[s1 * nl + li][p] * I1[s2][p] * I1[s3][p];
+                                if (cube) v += F[s1 * nl + li][p] * D[s2][p] * D[s3][p];
+                            }
+                            den[n * nl + li] = creal(u) / (double)n3;
+                            num[n * nl + li] = creal(v) / (double)n3;
+                        }
+                    }
+                    ++n;
+                }
+        for (int s = 0; s < ns; ++s) {
+            free(D[s]); free(I1[s]);
+            for (int li = 0; li < nl; ++li) { free(F[s * nl + li]); free(G[s * nl + li]); }
+        }
+        free(D); free(I1); free(F); free(G);
+    } else {
+        /* direct: every ordered pair of modes (k1, k2), k3 = -k1 - k2 */
+        long nt3 = (long)ns * ns * ns;
+        double *acc_n = calloc((size_t)nt3 * nl, sizeof(double)), *acc_d = calloc((size_t)nt3 * nl, sizeof(double));
+        double *acc_c = calloc((size_t)nt3, sizeof(double));
+        for (long p1 = 0; p1 < n3; ++p1) {
+            int s1 = S.idx[p1];
+            if (s1 < 1) continue;
+            long a1 = p1 / ((long)ng * ng), b1 = (p1 / ng) % ng, c1 = p1 % ng;
+            long i1 = signed_freq(a1, ng), j1 = signed_freq(b1, ng), n1 = signed_freq(c1, ng);
+            double y[8];
+            for (int li = 0; li < nl; ++li) y[li] = y_l0_at(2 * li, ng, a1, b1, c1);
+            for (long p2 = 0; p2 < n3; ++p2) {
+                int s2 = S.idx[p2];
+                if (s2 < 1 || s2 > s1) continue;
+                long a2 = p2 / ((long)ng * ng), b2 = (p2 / ng) % ng, c2 = p2 % ng;
+                long i3 = -i1 - signed_freq(a2, ng), j3 = -j1 - signed_freq(b2, ng), n3z = -n1 - signed_freq(c2, ng);
+                long h = ng / 2;
+                if (i3 < -h || i3 >= h || j3 < -h || j3 >= h || n3z < -h || n3z >= h) continue;
+                long p3 = (((i3 + ng) % ng) * ng + (j3 + ng) % ng) * ng + (n3z + ng) % ng;
+                int s3 = S.idx[p3];
+                if (s3 < 1 || s3 > s2) continue;
+                long t = ((long)s1 * ns + s2) * ns + s3;
+                acc_c[t] += 1.0;
+                cplx v = cube ? cube[p1] * cube[p2] * cube[p3] : 0;
+                for (int li = 0; li < nl; ++li) {
+                    acc_d[t * nl + li] += y[li] * y[li];
+                    acc_n[t * nl + li] += y[li] * creal(v);
+                }
+            }
+        }
+        for (int s1 = 1; s1 < ns; ++s1)
+            for (int s2 = 1; s2 <= s1; ++s2)
+                for (int s3 = 1; s3 <= s2; ++s3) {
+                    geom_t g;
+                    long t = ((long)s1 * ns + s2) * ns + s3;
+                    if (!combo_geometry(d, S.K[s1], S.K[s2], S.K[s3], 0, 0, 0, &g)) continue;
+                    if (!(acc_c[t] > 0.5)) continue;
+                    if (n < cap) {
+                        tri[4 * n] = s1; tri[4 * n + 1] = s2; tri[4 * n + 2] = s3; tri[4 * n + 3] = g.bin;
+                        ntri[n] = acc_c[t];
+                        for (int li = 0; li < nl; ++li) {
+                            den[n * nl + li] = acc_d[t * nl + li];
+                            num[n * nl + li] = acc_n[t * nl + li];
+                        }
+                    }
+                    ++n;
+                }
+        free(acc_n); free(acc_d); free(acc_c);
+    }
+    free(cube);
+    free(S.idx);
+    return n;
+}
+
+/* B_l^0 [n_k1][n_mu][n_t][nl] of the shell estimator (mode as above). */
+long bo_shell_estimate(const bo_desc *d, const double *delta, double *B)
+{
+    long n = bo_shell_triples(d, delta, 0, NULL, NULL, NULL, NULL);
+    if (n < 0) return -1;
+    int nl = d->l_max / 2 + 1;
+    int *tri = malloc(sizeof(int) * 4 * (size_t)(n > 0 ? n : 1));
+    double *nt = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *num = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * nl);
+    double *den = malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * nl);
+    bo_shell_triples(d, delta, n, tri, nt, num, den);
+    long nbin = (long)d->n_k1 * d->n_mu * d->n_t;
+    double *sn = calloc((size_t)nbin * nl, sizeof(double)), *sd = calloc((size_t)nbin * nl, sizeof(double));
+    for (long k = 0; k < n; ++k)
+        for (int li = 0; li < nl; ++li) {
+            sn[(long)tri[4 * k + 3] * nl + li] += num[k * nl + li];
+            sd[(long)tri[4 * k + 3] * nl + li] += den[k * nl + li];
+        }
+    double V = d->box_len * d->box_len * d->box_len;
+    for (long b = 0; b < nbin; ++b)
+        for (int li = 0; li < nl; ++li) {
+            int l = 2 * li;
+            double dn = sd[b * nl + li];
+            B[b * nl + li] = dn > 0 ? sqrt((2.0 * l + 1.0) / (2.0 * BO_TWO_PI)) * sn[b * nl + li] / (V * dn) : NAN;
+        }
+    free(tri); free(nt); free(num); free(den); free(sn); free(sd);
+    return n;
+}

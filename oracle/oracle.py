@@ -76,6 +76,10 @@ def _load():
                                               C.c_double, dp]
             lib.bo_discrete_model.restype = C.c_long
             lib.bo_orientation.argtypes = [C.c_double, C.c_double, C.c_double, dp, dp]
+            lib.bo_shell_triples.argtypes = [C.POINTER(Desc), dp, C.c_long, ip, dp, dp, dp]
+            lib.bo_shell_triples.restype = C.c_long
+            lib.bo_shell_estimate.argtypes = [C.POINTER(Desc), dp, dp]
+            lib.bo_shell_estimate.restype = C.c_long
             _lib = lib
     return _lib
 
@@ -274,3 +278,35 @@ def orientation(mu1, mu2, mu):
     pz, px = C.c_double(), C.c_double()
     _load().bo_orientation(mu1, mu2, mu, C.byref(pz), C.byref(px))
     return pz.value, px.value
+
+
+def shell_triples(delta, ng, box_len, k1_edges, n_mu, n_t, l_max, direct=False, nthreads=0):
+    """Spherical-shell m = 0 estimator: accepted shell triples (s1 >= s2 >= s3)
+    with their bin, N_tri, num_l and den_l (l = 0, 2, .., l_max).  delta may
+    be None (counts and denominators only)."""
+    desc, keep = _desc(ng, box_len, k1_edges, n_mu, n_t, l_max, direct, nthreads)
+    lib = _load()
+    d_arr = None if delta is None else np.ascontiguousarray(delta, dtype=np.float64)
+    dptr = _dp(d_arr) if d_arr is not None else C.cast(None, C.POINTER(C.c_double))
+    z = np.zeros(1)
+    n = lib.bo_shell_triples(C.byref(desc), dptr, 0, _ip(np.zeros(4, np.int32)), _dp(z), _dp(z), _dp(z))
+    if n < 0:
+        raise ValueError("invalid estimator parameters")
+    nl = l_max // 2 + 1
+    tri = np.zeros((max(n, 1), 4), dtype=np.int32)
+    nt = np.zeros(max(n, 1))
+    num = np.zeros((max(n, 1), nl))
+    den = np.zeros((max(n, 1), nl))
+    lib.bo_shell_triples(C.byref(desc), dptr, n, _ip(tri), _dp(nt), _dp(num), _dp(den))
+    return {"tri": tri[:n], "ntri": nt[:n], "num": num[:n], "den": den[:n]}
+
+
+def shell_estimate(delta, box_len, k1_edges, n_mu, n_t, l_max, direct=False, nthreads=0):
+    """B_l^0 [n_k1][n_mu][n_t][l_max/2 + 1] of the spherical-shell estimator."""
+    d_arr = np.ascontiguousarray(delta, dtype=np.float64)
+    ng = d_arr.shape[0]
+    desc, keep = _desc(ng, box_len, k1_edges, n_mu, n_t, l_max, direct, nthreads)
+    B = np.zeros((len(keep) - 1, n_mu, n_t, l_max // 2 + 1))
+    if _load().bo_shell_estimate(C.byref(desc), _dp(d_arr), _dp(B)) < 0:
+        raise ValueError("invalid estimator parameters")
+    return B
