@@ -52,6 +52,8 @@ WORKLOADS = {
     "c4": {"ng": 128, "box": 500.0, "nk1": 12, "nmu": 10, "mocks": 256, "batch": 16},
     # serving: a Poisson trace (20 requests/s) of mixed N_g, k1-bin runs and l_max
     "c5": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 10, "requests": 300, "rate": 20.0},
+    # the spherical-shell m = 0 estimator against the ring/plane estimator on c1's workload
+    "m0": {"ng": 64, "box": 1000.0, "nk1": 6, "nmu": 5, "shells": True},
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
@@ -531,6 +533,78 @@ def run_batched(args):
     return 0
 
 
+def run_shells(args):
+    """The spherical-shell estimator of the m = 0 multipoles (B_l^0 only)
+    against the ring/plane estimator (all 16 moments) on the same field and
+    bins: device time per estimate of each, and how their B_l^0 compare (the
+    two bin triangles differently, so they agree in expectation, not bin by
+    bin; on a point field both give a^3/V exactly)."""
+    import torch
+
+    from paper_2405_14513_gb300 import api, synth
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[args.workload]
+    ng = W["ng"]
+    cfg, edges = workload(W, "mixed_tc")
+    cfg["workload"] = cfg["workload"] + "; spherical shells (ring edges), m = 0"
+    shell = api.ShellPlan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX)
+    ring = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision="mixed_tc")
+    field = synth.make_field_torch(ng, W["box"], 1, device=dev).to(torch.float32).contiguous()
+    wss, wsr = shell.workspace(device=dev), ring.workspace(1, device=dev)
+    outs = torch.empty(shell.out_shape(), dtype=torch.float64, device=dev)
+    outr = torch.empty(ring.out_shape(1), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        t1.record(stream)
+        torch.cuda.synchronize(dev)
+        return t0.elapsed_time(t1) / args.steps
+
+    clocks = ClockSampler(index=0)
+    ms_s = timed(lambda: shell.estimate(field, wss, out=outs, stream=stream))
+    ms_r = timed(lambda: ring.estimate(field[None], wsr, out=outr, stream=stream))
+    clk = clocks.stop()
+    Bs = outs.cpu().numpy()
+    Br = outr.cpu().numpy()[0][..., [0, 1, 4, 9][: LMAX // 2 + 1]]      # the m = 0 moments, l = 0, 2, 4, 6
+    both = np.isfinite(Bs) & np.isfinite(Br)
+    agree = {}
+    for li in range(LMAX // 2 + 1):
+        a, b = Bs[..., li][both[..., li]], Br[..., li][both[..., li]]
+        scale = np.abs(b).max() if b.size else 1.0
+        agree[f"l={2 * li}"] = {"bins": int(b.size), "median_abs_diff_over_max": float(np.median(np.abs(a - b)) / scale),
+                                "correlation": float(np.corrcoef(a, b)[0, 1]) if b.size > 2 else None}
+    # point field: both give a^3/V
+    c = torch.zeros((ng, ng, ng), dtype=torch.float32, device=dev)
+    c[3, 5, 7] = 1.0
+    c -= 1.0 / ng ** 3
+    a3v = (W["box"] ** 3 / ng ** 3) ** 3 / W["box"] ** 3
+    ps = shell.estimate(c, wss).cpu().numpy()[..., 0]
+    pr = ring.estimate(c[None].contiguous(), wsr).cpu().numpy()[0][..., 0]
+    point = {"shell_max_rel_err": float(np.nanmax(np.abs(ps / a3v - 1))),
+             "ring_plane_max_rel_err": float(np.nanmax(np.abs(pr / a3v - 1)))}
+    n_bins = shell.n_k1 * shell.n_mu * shell.n_t
+    line = {"metric": f"B_l^0(k1,mu,t) configs/s at N_g={ng}, spherical shells (m = 0 only)",
+            "value": n_bins / (ms_s / 1e3), "unit": "configs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_s, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "clocks": clk,
+            "shells": {"n_shells": shell.n_shells, "n_triples": shell.n_triples, "moments": LMAX // 2 + 1},
+            "ring_plane": {"configs_per_s": n_bins / (ms_r / 1e3), "ms_per_step": ms_r, "moments": ring.n_lm},
+            "agreement_B_l0": agree, "point_field": point}
+    print(json.dumps(line), flush=True)
+    shell.close()
+    ring.close()
+    return 0
+
+
 def run_serving(args):
     """Serving (c5): the seeded 300-request Poisson trace through the serving
     loop (resident plans, continuous batching on 4 streams, HBM budget), then
@@ -585,7 +659,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
                     help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, "
-                         "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace")
+                         "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace; "
+                         "m0: the spherical-shell m = 0 estimator against the ring/plane one at 64^3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--split", default="replicas", choices=["replicas", "shares"],
                     help="N > 1: replicas (a field per rank, weak scaling; the default) or shares (one "
@@ -599,6 +674,8 @@ def main(argv=None):
         return run_batched(args)
     if "requests" in WORKLOADS[args.workload]:
         return run_serving(args)
+    if "shells" in WORKLOADS[args.workload]:
+        return run_shells(args)
     return run_ours(args)
 
 

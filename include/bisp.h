@@ -224,6 +224,36 @@ const char *estimator_status_string(int status);
 /* Description of the last failure on the calling thread ("" if none). */
 const char *estimator_last_error(void);
 
+/* ---------------- spherical-shell estimator of the m = 0 multipoles ---------------- */
+
+/* A comparison for the m = 0 subset.  The shell-based FFT estimators the
+ * paper builds on (Sec. I) bin modes in spherical shells and weight each
+ * mode by its own direction, which reaches only the m = 0 moments:
+ *   shells  s = {k : e_s <= |k| < e_{s+1}} (3D |k|, the ring edges of Sec. II);
+ *   triples s1 >= s2 >= s3 >= 1, binned in (k1, mu, t) from the shells' mean
+ *           radii as a ring combination is, kept when N_tri > 0;
+ *   num_l = sum Y_l0(k1) Delta(k1) Delta(k2) Delta(k3), den_l = sum Y_l0(k1)^2
+ *           over closed triangles with k_i in s_i (on the N_g^3 grid);
+ *   B_l^0 = sqrt((2l+1)/4pi) sum num_l / (V sum den_l) per bin (even l), NaN
+ *           where the denominator is 0.
+ * desc as for estimator_plan except: N_g <= 128, l_max <= 6, precision,
+ * max_batch and per-l grids ignored (FP32 fields and products, FP64 sums;
+ * FP64 plan-time counts and denominators).  B: DEVICE [n_k1][n_mu][n_t]
+ * [l_max/2 + 1].  delta: DEVICE float [N_g][N_g][N_g].  workspace: DEVICE,
+ * estimator_shell_info's workspace_bytes, 256-byte aligned.  (The paper
+ * has no counterpart in its own method; it cites this family.) */
+typedef struct bisp_shell_plan bisp_shell_plan;
+int estimator_shell_plan(bisp_shell_plan **out, const bisp_desc *desc, void *stream);
+int estimator_shell_info(const bisp_shell_plan *plan, int *n_shells, int64_t *n_triples, size_t *workspace_bytes);
+int estimator_shell_estimate(bisp_shell_plan *plan, const float *delta, void *workspace, double *B, void *stream);
+/* Accepted triples, HOST pointers (each may be NULL): tri [n][4] = s1, s2,
+ * s3, flat (k1, mu, t) bin; ntri [n]; den [n][l_max/2 + 1]. */
+int estimator_shell_triples(const bisp_shell_plan *plan, int32_t *tri, double *ntri, double *den);
+/* After estimator_shell_estimate on this workspace: num [n][l_max/2 + 1]
+ * (HOST), synchronising `stream`. */
+int estimator_shell_sums(const bisp_shell_plan *plan, const void *workspace, double *num, void *stream);
+void estimator_shell_destroy(bisp_shell_plan *plan);
+
 /* ---------------- estimate without caller-provided workspace ---------------- */
 
 /* estimator_estimate for callers that cannot allocate device memory: code

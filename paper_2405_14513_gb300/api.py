@@ -73,6 +73,18 @@ def load():
         lib.estimator_estimate_part.restype = C.c_int
         lib.estimator_stats_update.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp]
         lib.estimator_stats_update.restype = C.c_int
+        lib.estimator_shell_plan.argtypes = [C.POINTER(vp), C.POINTER(Desc), vp]
+        lib.estimator_shell_plan.restype = C.c_int
+        lib.estimator_shell_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_size_t)]
+        lib.estimator_shell_info.restype = C.c_int
+        lib.estimator_shell_estimate.argtypes = [vp, vp, vp, vp, vp]
+        lib.estimator_shell_estimate.restype = C.c_int
+        lib.estimator_shell_triples.argtypes = [vp, vp, vp, vp]
+        lib.estimator_shell_triples.restype = C.c_int
+        lib.estimator_shell_sums.argtypes = [vp, vp, vp, vp]
+        lib.estimator_shell_sums.restype = C.c_int
+        lib.estimator_shell_destroy.argtypes = [vp]
+        lib.estimator_shell_destroy.restype = None
         lib.estimator_destroy.argtypes = [vp]
         lib.estimator_destroy.restype = None
         lib.estimator_status_string.argtypes = [C.c_int]
@@ -352,6 +364,72 @@ class Plan:
         f = np.zeros(len(STAGES))
         _check(load().estimator_stage_flops(self._h, _dp(f)), "estimator_stage_flops")
         return dict(zip(STAGES, f.tolist()))
+
+
+class ShellPlan:
+    """The spherical-shell estimator of the m = 0 multipoles
+    (``estimator_shell_*``): B_l^0 [n_k1][n_mu][n_t][l_max/2 + 1]."""
+
+    def __init__(self, n_g: int, box_len: float, k1_edges, n_mu: int, n_t: int, l_max: int, stream=None):
+        lib = load()
+        self._edges = np.ascontiguousarray(k1_edges, dtype=np.float64)
+        self.n_g, self.box_len, self.n_mu, self.n_t, self.l_max = n_g, box_len, n_mu, n_t, l_max
+        self.n_k1 = len(self._edges) - 1
+        self.nl = l_max // 2 + 1
+        d = Desc(n_g, box_len, self.n_k1, _dp(self._edges), n_mu, n_t, l_max, PRECISIONS["mixed"], 1)
+        h = C.c_void_p()
+        _check(lib.estimator_shell_plan(C.byref(h), C.byref(d), _stream_handle(stream) if stream is not None
+                                        else C.c_void_p(0)), "estimator_shell_plan")
+        self._h = h
+        ns, nt, wb = C.c_int(), C.c_int64(), C.c_size_t()
+        _check(lib.estimator_shell_info(h, C.byref(ns), C.byref(nt), C.byref(wb)), "estimator_shell_info")
+        self.n_shells, self.n_triples, self._ws_bytes = ns.value, nt.value, wb.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().estimator_shell_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def out_shape(self):
+        return (self.n_k1, self.n_mu, self.n_t, self.nl)
+
+    def workspace(self, device="cuda"):
+        import torch
+        return torch.empty(max(self._ws_bytes, 256), dtype=torch.uint8, device=device)
+
+    def estimate(self, delta, workspace, out=None, stream=None):
+        """delta: contiguous CUDA float32 [N][N][N]; returns CUDA float64 B_l^0."""
+        import torch
+        if delta.dtype != torch.float32 or not delta.is_cuda or not delta.is_contiguous() or \
+                tuple(delta.shape) != (self.n_g,) * 3:
+            raise ValueError("delta must be a contiguous CUDA float32 [N][N][N] of the plan's grid")
+        if out is None:
+            out = torch.empty(self.out_shape(), dtype=torch.float64, device=delta.device)
+        _check(load().estimator_shell_estimate(self._h, C.c_void_p(delta.data_ptr()), C.c_void_p(workspace.data_ptr()),
+                                               C.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "estimator_shell_estimate")
+        return out
+
+    def triples(self):
+        n = self.n_triples
+        tri = np.zeros((max(n, 1), 4), dtype=np.int32)
+        nt = np.zeros(max(n, 1))
+        den = np.zeros((max(n, 1), self.nl))
+        _check(load().estimator_shell_triples(self._h, C.c_void_p(tri.ctypes.data), C.c_void_p(nt.ctypes.data),
+                                              C.c_void_p(den.ctypes.data)), "estimator_shell_triples")
+        return {"tri": tri[:n], "ntri": nt[:n], "den": den[:n]}
+
+    def sums(self, workspace, stream=None):
+        num = np.zeros((max(self.n_triples, 1), self.nl))
+        _check(load().estimator_shell_sums(self._h, C.c_void_p(workspace.data_ptr()), C.c_void_p(num.ctypes.data),
+                                           _stream_handle(stream)), "estimator_shell_sums")
+        return num[: self.n_triples]
 
 
 STAGES = ["forward", "step1", "step2", "reduce", "bin"]

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbisp.so")
-SOURCES = ["plan.cpp", "kernels.cu", "step2_tc.cu", "abi.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "step2_tc.cu", "abi.cu", "noalloc.cu", "shell.cu"]
 HEADERS = ["plan.hpp", "kernels.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -54,6 +54,8 @@ namespace bisp {
 // Record a failure message for estimator_last_error() from another
 // translation unit of the library.
 int record_error(int code, const char *msg) { return fail(code, msg); }
+// Clear the calling thread's failure message (at the entry of a call).
+void clear_error() { g_err.clear(); }
 }  // namespace bisp
 
 struct bisp_plan {
