@@ -477,9 +477,9 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     for (int r = 0; r < R.nr; ++r) p->ring_arg.maxc[r] = R.maxc[r];
 
     for (int l = 0; l < R.ngrid; ++l) p->grid_arg.M[l] = R.grid[l];
-    // twiddles in double: exp(-2 pi i k / 2^lg2), k < 3/4 of 2^lg2, for the
-    // lengths 2^q, and exp(-2 pi i k / (3 x 2^lg3)), k < 3/4 of 3 x 2^lg3, for
-    // 3 x 2^q (three quarters of the circle: radix-4 stages reach it)
+    // twiddles in double: exp(-2 pi i k / 2^lg2), k < 7/8 of 2^lg2, for the
+    // lengths 2^q, and exp(-2 pi i k / (3 x 2^lg3)), k < 7/8 of 3 x 2^lg3, for
+    // 3 x 2^q (seven eighths of the circle: radix-8 stages reach it)
     {
         // lengths 2^q <= N_g use exp(-2 pi i k / 2^lg2); lengths 3 x 2^q <= N_g
         // use exp(-2 pi i k / (3 x 2^lg3))
@@ -501,8 +501,8 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
         };
         float2 *f2 = nullptr, *f3 = nullptr;
         double2 *d2 = nullptr, *d3 = nullptr;
-        int st = table(1 << lg2, (3 * (1 << lg2) + 3) / 4, &f2, &d2);
-        if (!st) st = table(3 << lg3, (3 * (3 << lg3) + 3) / 4, &f3, &d3);
+        int st = table(1 << lg2, (7 * (1 << lg2) + 7) / 8, &f2, &d2);
+        if (!st) st = table(3 << lg3, (7 * (3 << lg3) + 7) / 8, &f3, &d3);
         if (st) return st;
         p->tw_f = Twiddles<float2>{f2, f3, lg2, lg3};
         p->tw_d = Twiddles<double2>{d2, d3, lg2, lg3};

@@ -77,8 +77,8 @@ struct DivIter {
 
 // Stockham transform of nrows rows of length M = 2^q or 3 x 2^q held in
 // shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M): one
-// radix-3 stage first when 3 divides M, then radix-4 stages and, for an odd
-// power of two, one radix-2 stage.  Every thread
+// radix-3 stage first when 3 divides M, then radix-8 stages and, for what
+// is left of the power of two, one radix-4 or radix-2 stage.  Every thread
 // of the block takes part; the caller synchronises before the call.  The
 // result is in the returned buffer (a or b).
 template <typename C>
@@ -117,7 +117,57 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
     const int lg = has3 ? tw.lg3 : tw.lg2;
     int s = 0;                                  // Ns = 2^s (times 3 if has3)
     while (Ns < M) {
-        if (M / Ns >= 4) {
+        if (M / Ns >= 8) {
+            // radix 8: v_r = x[j + r M/8] w^(rk), w = exp(-2 pi i / (8 Ns)),
+            // out[q 8 Ns + k + m Ns] = sum_r v_r exp(-2 pi i rm / 8), as a
+            // radix-2 step (pairs r, r + 4; the odd half turned by
+            // exp(-2 pi i r / 8)) followed by two 4-point transforms
+            const int eighth = M / 8;
+            const int total = nrows * eighth;
+            const int sh = lg - s - 3;
+            const Rr r2 = Rr(0.70710678118654752440);   // 1/sqrt(2)
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                const int row = has3 ? int(unsigned(t >> (p - 3)) / 3u) : (t >> (p - 3));
+                const int j = t - row * eighth;
+                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int k = j - q * Ns;
+                const C *src = a + row * P + j;
+                C v[8];
+                v[0] = src[0];
+#pragma unroll
+                for (int r = 1; r < 8; ++r) v[r] = cmul(src[r * eighth], __ldg(&wt[(r * k) << sh]));
+                C e[4], o[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    e[r] = cadd(v[r], v[r + 4]);
+                    o[r] = csub(v[r], v[r + 4]);
+                }
+                // o_1 exp(-i pi/4), o_2 (-i), o_3 exp(-3 i pi/4)
+                {
+                    const C t1 = o[1], t3 = o[3];
+                    o[1].x = (t1.x + t1.y) * r2; o[1].y = (t1.y - t1.x) * r2;
+                    const Rr x2 = o[2].x;
+                    o[2].x = o[2].y; o[2].y = -x2;
+                    o[3].x = (t3.y - t3.x) * r2; o[3].y = -(t3.x + t3.y) * r2;
+                }
+                C *dst = b + row * P + q * 8 * Ns + k;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const C *x = h ? o : e;
+                    const C s02 = cadd(x[0], x[2]), d02 = csub(x[0], x[2]), s13 = cadd(x[1], x[3]),
+                            d13 = csub(x[1], x[3]);
+                    C m1 = d02, m3 = d02;                 // d02 -/+ i d13
+                    m1.x += d13.y; m1.y -= d13.x;
+                    m3.x -= d13.y; m3.y += d13.x;
+                    dst[(0 + h) * Ns] = cadd(s02, s13);
+                    dst[(2 + h) * Ns] = m1;
+                    dst[(4 + h) * Ns] = csub(s02, s13);
+                    dst[(6 + h) * Ns] = m3;
+                }
+            }
+            Ns *= 8;
+            s += 3;
+        } else if (M / Ns >= 4) {
             // radix 4: v_r = x[j + r M/4] w^(rk), w = exp(-2 pi i / (4 Ns)),
             // out[q 4 Ns + k + m Ns] = sum_r v_r (-i)^(rm)
             const int quarter = M / 4;

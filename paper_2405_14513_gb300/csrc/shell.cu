@@ -272,8 +272,8 @@ int make_twiddles(bisp_shell_plan *p, cudaStream_t s)
         int st = sup(p, d, vd, s);
         return st ? st : sup(p, f, vf, s);
     };
-    int st = table(1 << lg2, (3 * (1 << lg2) + 3) / 4, &p->tw2f, &p->tw2d);
-    if (!st) st = table(3 << lg3, (3 * (3 << lg3) + 3) / 4, &p->tw3f, &p->tw3d);
+    int st = table(1 << lg2, (7 * (1 << lg2) + 7) / 8, &p->tw2f, &p->tw2d);
+    if (!st) st = table(3 << lg3, (7 * (3 << lg3) + 7) / 8, &p->tw3f, &p->tw3d);
     if (st) return st;
     p->twf = Twiddles<float2>{p->tw2f, p->tw3f, lg2, lg3};
     p->twd = Twiddles<double2>{p->tw2d, p->tw3d, lg2, lg3};
