@@ -56,6 +56,7 @@
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -798,6 +799,327 @@ long bo_estimate_part(const bo_desc *d, const double *delta, int part, int npart
 {
     if (nparts < 1 || part < 0 || part >= nparts) return -1;
     return estimate_share(d, delta, part, nparts, B, NULL, NULL, NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* The estimate of bo_estimate for grids whose D fields do not all fit in    */
+/* memory (N_g = 512: 341 planes x 42 rings x N_g^2 complex doubles, 60 GB), */
+/* in slabs of n1 with a checkpoint after each slab.                         */
+/*                                                                          */
+/* Two facts of the definitions let it keep the planes n >= 0 only:          */
+/*  - delta is real, so Delta(-k) = conj Delta(k); a ring is symmetric under */
+/*    u -> -u (its radius stays below N_g/3, short of the Nyquist index), so */
+/*    Eq. iFT gives D(r, -n, x) = conj D(r, n, x);                           */
+/*  - so the combination (-n1, -n2, -n3; r1, r2, r3) has the sum conj S of   */
+/*    (n1, n2, n3; r1, r2, r3) in Eq. fftbs, and the same acceptance and bin */
+/*    (these depend on n_i^2 only); its weight Y* is its own (p_z and p_x    */
+/*    change sign), computed by combo_geometry like every other.            */
+/* Slab n1 (n1 = 0, 1, .., floor(N_g/3)) forms S for every accepted          */
+/* (n1, n2; r1, r2, r3), n2 over all planes, and adds to num and den both   */
+/* that combination and, for n1 > 0, its mirror with conj S: every ordered  */
+/* combination of bo_estimate is counted once.  Each S is the running sum   */
+/* S += (D1 D2) D3 over x in increasing order, as in bo_estimate; x is cut  */
+/* into chunks and D1 D2 of a chunk is formed once for the r3 that share    */
+/* (r1, r2), which changes no operation of any one sum.  The accumulation   */
+/* into num and den differs from bo_estimate's only in order.               */
+/*                                                                          */
+/* ckpt (may be NULL): after every slab, num, den and the next slab are      */
+/* written there (via a temporary file and a rename); a later call with the */
+/* same parameters and field resumes after the last finished slab.  The    */
+/* field is identified by a weighted sum of its values stored in the file. */
+/* Outputs as bo_estimate.  Returns the number of accepted ordered          */
+/* combinations, or -1 (bad parameters, no memory, unreadable checkpoint). */
+/* max_slabs > 0 stops after that many slabs of this call and returns -2   */
+/* once their checkpoint is written (the outputs are then not set).        */
+/* verbose: one line per slab on stderr.                                    */
+/* ------------------------------------------------------------------------ */
+#define BO_CKPT_MAGIC 0x31304b4350434f42L  /* "BOCPCK01" */
+
+typedef struct { int n2, n3, r1, r2, r3; long ntri; } stream_combo_t;
+
+static double field_tag(const double *delta, long n)
+{
+    double s = 0;
+    for (long i = 0; i < n; ++i) s += delta[i] * (double)(1 + i % 1021);
+    return s;
+}
+
+static int ckpt_header_ok(FILE *f, const bo_desc *d, double tag)
+{
+    long magic;
+    int h[5];
+    double bl, tg;
+    if (fread(&magic, sizeof magic, 1, f) != 1 || magic != BO_CKPT_MAGIC) return 0;
+    if (fread(h, sizeof(int), 5, f) != 5) return 0;
+    if (h[0] != d->ng || h[1] != d->n_k1 || h[2] != d->n_mu || h[3] != d->n_t || h[4] != d->l_max) return 0;
+    if (fread(&bl, sizeof bl, 1, f) != 1 || bl != d->box_len) return 0;
+    for (int b = 0; b <= d->n_k1; ++b) {
+        double e;
+        if (fread(&e, sizeof e, 1, f) != 1 || e != d->k1_edges[b]) return 0;
+    }
+    if (fread(&tg, sizeof tg, 1, f) != 1 || tg != tag) return 0;
+    return 1;
+}
+
+static int ckpt_write(const char *path, const bo_desc *d, double tag, int next_slab, long ncombo,
+                      const cplx *num, const double *dn, long nel)
+{
+    size_t len = strlen(path);
+    char *tmp = malloc(len + 8);
+    memcpy(tmp, path, len);
+    memcpy(tmp + len, ".tmp", 5);
+    FILE *f = fopen(tmp, "wb");
+    if (!f) { free(tmp); return -1; }
+    long magic = BO_CKPT_MAGIC;
+    int h[5] = {d->ng, d->n_k1, d->n_mu, d->n_t, d->l_max};
+    int ok = fwrite(&magic, sizeof magic, 1, f) == 1 && fwrite(h, sizeof(int), 5, f) == 5 &&
+             fwrite(&d->box_len, sizeof(double), 1, f) == 1 &&
+             fwrite(d->k1_edges, sizeof(double), (size_t)d->n_k1 + 1, f) == (size_t)d->n_k1 + 1 &&
+             fwrite(&tag, sizeof tag, 1, f) == 1 && fwrite(&next_slab, sizeof(int), 1, f) == 1 &&
+             fwrite(&ncombo, sizeof(long), 1, f) == 1 &&
+             fwrite(num, sizeof(cplx), (size_t)nel, f) == (size_t)nel &&
+             fwrite(dn, sizeof(double), (size_t)nel, f) == (size_t)nel;
+    ok = (fclose(f) == 0) && ok;
+    if (ok) ok = rename(tmp, path) == 0;
+    free(tmp);
+    return ok ? 0 : -1;
+}
+
+/* The accepted combinations of the ordered plane pair (n1, n2), in (r1, r2, r3) order. */
+static long pair_combos(const bo_desc *d, const rings_t *R, const long *ntri, int n1, int n2,
+                        stream_combo_t *out)
+{
+    int nr = R->nr, n3 = -(n1 + n2);
+    long k = 0;
+    for (int r1 = 0; r1 < nr; ++r1)
+        for (int r2 = 0; r2 < nr; ++r2)
+            for (int r3 = 0; r3 < nr; ++r3) {
+                long nt = ntri[((long)r1 * nr + r2) * nr + r3];
+                if (nt <= 0) continue;
+                geom_t g;
+                if (!combo_geometry(d, R->kperp[r1], R->kperp[r2], R->kperp[r3], n1, n2, n3, &g)) continue;
+                out[k].n2 = n2; out[k].n3 = n3;
+                out[k].r1 = r1; out[k].r2 = r2; out[k].r3 = r3;
+                out[k].ntri = nt;
+                ++k;
+            }
+    return k;
+}
+
+/* D(r, n) of the store of planes n >= 0, conjugated for n < 0 (cj = 1). */
+static const cplx *stored_field(const cplx *D, int nr, long np, int r, int n, int *cj)
+{
+    *cj = n < 0;
+    return D + ((long)(n < 0 ? -n : n) * nr + r) * np;
+}
+
+/* Sums S_k = sum_x D(r1,n1) D(r2,n2) D(r3,n3) of one plane pair's combinations. */
+static void pair_sums(const cplx *D, int nr, long np, int n1, const stream_combo_t *c, long nc, cplx *S, cplx *P)
+{
+    enum { XC = 512 };
+    for (long k = 0; k < nc; ++k) S[k] = 0;
+    for (long x0 = 0; x0 < np; x0 += XC) {
+        long xn = np - x0 < XC ? np - x0 : XC;
+        long k = 0;
+        while (k < nc) {
+            long kend = k;
+            while (kend < nc && c[kend].r1 == c[k].r1 && c[kend].r2 == c[k].r2) ++kend;
+            int ca, cb;
+            const cplx *a = stored_field(D, nr, np, c[k].r1, n1, &ca) + x0;
+            const cplx *b = stored_field(D, nr, np, c[k].r2, c[k].n2, &cb) + x0;
+            for (long x = 0; x < xn; ++x) {
+                cplx av = ca ? conj(a[x]) : a[x], bv = cb ? conj(b[x]) : b[x];
+                P[x] = av * bv;
+            }
+            /* up to four r3 at a time, each its own running sum: the
+             * product P e written out as (pr er - pi ei) + i (pr ei + pi er),
+             * the operations of the complex product, with ei negated (exact)
+             * for a conjugated field */
+            while (k < kend) {
+                const int nk = kend - k < 4 ? (int)(kend - k) : 4;
+                const double *e[4];
+                double sr[4], si[4], sg = 1.0;
+                for (int j = 0; j < 4; ++j) {
+                    int ce;
+                    const int kk = j < nk ? (int)(k + j) : (int)k;
+                    e[j] = (const double *)(stored_field(D, nr, np, c[kk].r3, c[kk].n3, &ce) + x0);
+                    sg = ce ? -1.0 : 1.0;           /* the same n3 for every combination of the pair */
+                    sr[j] = creal(S[kk]);
+                    si[j] = cimag(S[kk]);
+                }
+                const double *p = (const double *)P;
+                if (nk == 4) {
+                    for (long x = 0; x < xn; ++x) {
+                        const double pr = p[2 * x], pi = p[2 * x + 1];
+                        for (int j = 0; j < 4; ++j) {
+                            const double er = e[j][2 * x], ei = sg * e[j][2 * x + 1];
+                            sr[j] = sr[j] + (pr * er - pi * ei);
+                            si[j] = si[j] + (pr * ei + pi * er);
+                        }
+                    }
+                } else {
+                    for (long x = 0; x < xn; ++x) {
+                        const double pr = p[2 * x], pi = p[2 * x + 1];
+                        for (int j = 0; j < nk; ++j) {
+                            const double er = e[j][2 * x], ei = sg * e[j][2 * x + 1];
+                            sr[j] = sr[j] + (pr * er - pi * ei);
+                            si[j] = si[j] + (pr * ei + pi * er);
+                        }
+                    }
+                }
+                for (int j = 0; j < nk; ++j) S[k + j] = CMPLX(sr[j], si[j]);
+                k += nk;
+            }
+        }
+    }
+}
+
+static void add_combo(const bo_desc *d, const rings_t *R, int n1, const stream_combo_t *c, cplx S, double norm,
+                      int nlm, cplx *num, double *dn)
+{
+    geom_t g;
+    combo_geometry(d, R->kperp[c->r1], R->kperp[c->r2], R->kperp[c->r3], n1, c->n2, c->n3, &g);
+    for (int l = 0; l <= d->l_max; ++l)
+        for (int m = 0; m <= l; ++m) {
+            long o = (long)g.bin * nlm + lm_index(l, m);
+            num[o] += combo_ystar(l, m, &g) * S * norm;
+            dn[o] += (double)c->ntri * combo_y2(l, m, &g);
+        }
+}
+
+long bo_estimate_stream(const bo_desc *d, const double *delta, const char *ckpt, int max_slabs, int verbose,
+                        double *B, double *num_re, double *num_im, double *den)
+{
+    if (desc_check(d) || d->mode != 0 || (max_slabs > 0 && !ckpt)) return -1;
+    set_threads(d->nthreads);
+    rings_t R;
+    if (rings_build(d->ng, &R)) return -1;
+    int ng = d->ng, nr = R.nr, nz = R.nz;
+    long np = (long)ng * ng;
+    int nlm = n_moments_all(d->l_max);
+    long nbin = (long)d->n_k1 * d->n_mu * d->n_t, nel = nbin * nlm;
+    double V = d->box_len * d->box_len * d->box_len;
+    double norm = 1.0 / (V * (double)ng * (double)ng);
+    double tag = field_tag(delta, np * ng);
+
+    cplx *num = calloc((size_t)nel, sizeof(cplx));
+    double *dn = calloc((size_t)nel, sizeof(double));
+    long ncombo = 0;
+    int slab0 = 0;
+    if (ckpt) {
+        FILE *f = fopen(ckpt, "rb");
+        if (f) {
+            int ok = ckpt_header_ok(f, d, tag) && fread(&slab0, sizeof(int), 1, f) == 1 &&
+                     fread(&ncombo, sizeof(long), 1, f) == 1 &&
+                     fread(num, sizeof(cplx), (size_t)nel, f) == (size_t)nel &&
+                     fread(dn, sizeof(double), (size_t)nel, f) == (size_t)nel;
+            fclose(f);
+            if (!ok) { free(num); free(dn); free(R.ringidx); return -1; }
+            if (verbose) fprintf(stderr, "stream: resuming at slab %d of %d\n", slab0, nz + 1);
+        }
+    }
+
+    long *ntri = malloc(sizeof(long) * (size_t)nr * nr * nr);
+    ntri_fft(&R, ntri);
+    cplx *D = NULL;
+    if (slab0 <= nz) {
+        cplx *cube = forward_cube(ng, d->box_len, delta);
+        D = cube ? malloc(sizeof(cplx) * (size_t)(nz + 1) * nr * np) : NULL;
+        if (!D) { free(cube); free(ntri); free(num); free(dn); free(R.ringidx); return -1; }
+#pragma omp parallel for schedule(dynamic)
+        for (long f = 0; f < (long)(nz + 1) * nr; ++f)
+            dfield_from_cube(&R, cube, (int)(f % nr), (int)(f / nr), D + f * np);
+        free(cube);
+        if (verbose) fprintf(stderr, "stream: %ld D fields ready\n", (long)(nz + 1) * nr);
+    }
+
+    int nth = 1;
+#ifdef _OPENMP
+    nth = omp_get_max_threads();
+#endif
+    cplx *tnum = calloc((size_t)nth * nel, sizeof(cplx));
+    double *tdn = calloc((size_t)nth * nel, sizeof(double));
+    long cap = (long)nr * nr * nr;
+    int failed = 0, stopped = 0;
+    for (int n1 = slab0; n1 <= nz && !failed; ++n1) {
+        if (max_slabs > 0 && n1 - slab0 >= max_slabs) { stopped = 1; break; }
+        double t0 = 0;
+#ifdef _OPENMP
+        t0 = omp_get_wtime();
+#endif
+        long slab_combos = 0;
+        memset(tnum, 0, sizeof(cplx) * (size_t)nth * nel);
+        memset(tdn, 0, sizeof(double) * (size_t)nth * nel);
+#pragma omp parallel reduction(+ : slab_combos)
+        {
+            int me = 0;
+#ifdef _OPENMP
+            me = omp_get_thread_num();
+#endif
+            stream_combo_t *c = malloc(sizeof(stream_combo_t) * (size_t)cap);
+            cplx *S = malloc(sizeof(cplx) * (size_t)cap);
+            cplx *P = malloc(sizeof(cplx) * 512);
+            cplx *mynum = tnum + (long)me * nel;
+            double *mydn = tdn + (long)me * nel;
+            /* round robin over n2: for a given thread count every thread
+             * sums the same pairs in the same order, so a resumed run ends
+             * with the bits of an uninterrupted one */
+#pragma omp for schedule(static, 1)
+            for (int n2 = -nz; n2 <= nz; ++n2) {
+                int n3 = -(n1 + n2);
+                if (n3 < -nz || n3 > nz) continue;
+                long nc = pair_combos(d, &R, ntri, n1, n2, c);
+                if (nc == 0) continue;
+                pair_sums(D, nr, np, n1, c, nc, S, P);
+                for (long k = 0; k < nc; ++k) {
+                    add_combo(d, &R, n1, &c[k], S[k], norm, nlm, mynum, mydn);
+                    slab_combos += 1;
+                    if (n1 > 0) {
+                        stream_combo_t m = c[k];
+                        m.n2 = -c[k].n2;
+                        m.n3 = -c[k].n3;
+                        add_combo(d, &R, -n1, &m, conj(S[k]), norm, nlm, mynum, mydn);
+                        slab_combos += 1;
+                    }
+                }
+            }
+            free(c);
+            free(S);
+            free(P);
+        }
+        for (int t = 0; t < nth; ++t)
+            for (long o = 0; o < nel; ++o) {
+                num[o] += tnum[(long)t * nel + o];
+                dn[o] += tdn[(long)t * nel + o];
+            }
+        ncombo += slab_combos;
+        if (ckpt && ckpt_write(ckpt, d, tag, n1 + 1, ncombo, num, dn, nel)) failed = 1;
+        if (verbose) {
+            double t1 = 0;
+#ifdef _OPENMP
+            t1 = omp_get_wtime();
+#endif
+            fprintf(stderr, "stream: slab %d/%d  %ld combinations  %.1f s\n", n1, nz, slab_combos, t1 - t0);
+        }
+    }
+    free(tnum);
+    free(tdn);
+    free(D);
+    free(ntri);
+    if (!failed && !stopped)
+        for (long b = 0; b < nbin; ++b)
+            for (int l = 0; l <= d->l_max; ++l)
+                for (int m = 0; m <= l; ++m) {
+                    long o = b * nlm + lm_index(l, m);
+                    if (num_re) num_re[o] = creal(num[o]);
+                    if (num_im) num_im[o] = cimag(num[o]);
+                    if (den) den[o] = dn[o];
+                    B[o] = dn[o] > 0 ? sqrt((2.0 * l + 1.0) / (2.0 * BO_TWO_PI)) * creal(num[o]) / dn[o] : NAN;
+                }
+    free(num);
+    free(dn);
+    free(R.ringidx);
+    return failed ? -1 : stopped ? -2 : ncombo;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -64,6 +64,8 @@ def _load():
             lib.bo_estimate.restype = C.c_long
             lib.bo_estimate_part.argtypes = [C.POINTER(Desc), dp, C.c_int, C.c_int, dp]
             lib.bo_estimate_part.restype = C.c_long
+            lib.bo_estimate_stream.argtypes = [C.POINTER(Desc), dp, C.c_char_p, C.c_int, C.c_int, dp, dp, dp, dp]
+            lib.bo_estimate_stream.restype = C.c_long
             lib.bo_combos.argtypes = [C.POINTER(Desc), C.c_int, C.c_long, ip, lp, ip, dp]
             lib.bo_combos.restype = C.c_long
             lib.bo_combo_sums.argtypes = [C.c_int, C.c_double, dp, C.c_long, ip, C.c_int, dp, dp]
@@ -209,6 +211,28 @@ def estimate_part(delta, box_len, k1_edges, n_mu, n_t, l_max, part, nparts, dire
     if _load().bo_estimate_part(C.byref(desc), _dp(d_arr), int(part), int(nparts), _dp(B)) < 0:
         raise ValueError("invalid estimator parameters")
     return B
+
+
+def estimate_stream(delta, box_len, k1_edges, n_mu, n_t, l_max, ckpt=None, max_slabs=0, verbose=False,
+                    nthreads=0):
+    """estimate(...) in slabs of n1 with the D fields of the planes n >= 0 only
+    (D(r, -n) = conj D(r, n) for a real field) and, if ``ckpt`` is a path, a
+    checkpoint after each slab from which a later call resumes.  With
+    ``max_slabs`` > 0 it stops after that many slabs and returns None."""
+    d_arr = np.ascontiguousarray(delta, dtype=np.float64)
+    ng = d_arr.shape[0]
+    desc, keep = _desc(ng, box_len, k1_edges, n_mu, n_t, l_max, False, nthreads)
+    shape = (len(keep) - 1, n_mu, n_t, n_moments_all(l_max))
+    B = np.zeros(shape)
+    nr_, ni_, dn_ = np.zeros(shape), np.zeros(shape), np.zeros(shape)
+    path = None if ckpt is None else os.fsencode(ckpt)
+    nc = _load().bo_estimate_stream(C.byref(desc), _dp(d_arr), path, int(max_slabs), 1 if verbose else 0,
+                                    _dp(B), _dp(nr_), _dp(ni_), _dp(dn_))
+    if nc == -2:
+        return None
+    if nc < 0:
+        raise ValueError("invalid estimator parameters, no memory, or a checkpoint of another run")
+    return {"B": B, "num_re": nr_, "num_im": ni_, "den": dn_, "n_combos": int(nc)}
 
 
 def select_even(arr: np.ndarray, l_max: int) -> np.ndarray:

@@ -193,3 +193,36 @@ def test_combination_geometry_against_explicit_triangles():
         assert abs(cphi - p[0] / np.hypot(p[0], p[1])) < 1e-8
         checked += 1
     assert checked > 100
+
+
+@pytest.mark.parametrize("ng,n_k1,nmu", [(16, 3, 4), (32, 5, 5), (48, 6, 5)])
+def test_streamed_estimate_equals_plain_estimate(ng, n_k1, nmu):
+    """The slab-streamed oracle (planes n >= 0 stored, D(r,-n) = conj D(r,n),
+    mirrored combinations from conj S) gives the plain estimate of every
+    ordered combination to FP64 rounding."""
+    d, L, e, _, _ = _case(ng, n_k1, nmu, nmu, seed=4)
+    a = O.estimate(d, L, e, nmu, nmu, L_MAX)
+    b = O.estimate_stream(d, L, e, nmu, nmu, L_MAX)
+    assert a["n_combos"] == b["n_combos"] > 0
+    for key in ("num_re", "num_im", "den"):
+        assert np.abs(a[key] - b[key]).max() <= 1e-13 * np.abs(a[key]).max(), key
+    fin = np.isfinite(a["B"])
+    assert np.array_equal(fin, np.isfinite(b["B"]))
+    assert np.abs(a["B"][fin] - b["B"][fin]).max() <= 1e-13 * np.abs(a["B"][fin]).max()
+
+
+def test_streamed_estimate_resumes_from_checkpoint(tmp_path):
+    """Stopped after some slabs and resumed from its checkpoint, the streamed
+    oracle ends with the result of one uninterrupted run; a checkpoint of
+    another field is refused."""
+    d, L, e, nmu, nt = _case(32, 4, 5, 5, seed=6)
+    whole = O.estimate_stream(d, L, e, nmu, nt, L_MAX, nthreads=2)
+    ck = str(tmp_path / "run.ckpt")
+    assert O.estimate_stream(d, L, e, nmu, nt, L_MAX, ckpt=ck, max_slabs=3, nthreads=2) is None
+    assert O.estimate_stream(d, L, e, nmu, nt, L_MAX, ckpt=ck, max_slabs=4, nthreads=2) is None
+    part = O.estimate_stream(d, L, e, nmu, nt, L_MAX, ckpt=ck, nthreads=2)
+    assert part["n_combos"] == whole["n_combos"]
+    for key in ("num_re", "num_im", "den"):
+        assert np.array_equal(part[key], whole[key]), key
+    with pytest.raises(ValueError):
+        O.estimate_stream(d * 1.5, L, e, nmu, nt, L_MAX, ckpt=ck, nthreads=2)
