@@ -42,8 +42,9 @@
  *     ties are accepted once per valid labelling;
  *   - mu = (K1^2+K2^2-K3^2)/(2 K1 K2), which lies in [1/2, 1] when
  *     K1 >= K2 >= K3 (clamped there against rounding); t = K2/K1;
- *   - mu and t bins are uniform on [0.5, 1]: index floor((x-0.5)*2n), top
- *     edge closed; t < 0.5 is dropped;
+ *   - mu and t bins are uniform on [0.5, 1]: bin j holds
+ *     1/2 + j/(2n) <= x < 1/2 + (j+1)/(2n), top edge closed; t < 0.5 is
+ *     dropped;
  *   - the two chiralities (p_y = +/-) of every combination are averaged;
  *     p_y = +sqrt(max(0, 1 - p_z^2 - p_x^2)); for mu >= 1 - 1e-12 the
  *     azimuth is undefined and Y* is averaged over it;
@@ -552,6 +553,16 @@ static void orient_inverse(double mu1, double mu2, double mu, double *pz, double
     *px = (mu2 + mu * mu1) / sqrt(1.0 - mu * mu);
 }
 
+/* Bin of x among n uniform bins of [1/2, 1]: bin j holds
+ * 1/2 + j/(2n) <= x < 1/2 + (j+1)/(2n), and the top edge x = 1 belongs to
+ * the last bin. */
+static int half_unit_bin(double x, int n)
+{
+    int j = 0;
+    while (j + 1 < n && 0.5 + (double)(j + 1) / (2.0 * n) <= x) ++j;
+    return j;
+}
+
 /* Returns 1 when the combination is accepted into a (k1, mu, t) bin. */
 static int combo_geometry(const bo_desc *d, double kp1, double kp2, double kp3,
                           int n1, int n2, int n3, geom_t *g)
@@ -577,10 +588,8 @@ static int combo_geometry(const bo_desc *d, double kp1, double kp2, double kp3,
     if (mu < 0.5) mu = 0.5;
     g->mu = mu;
     if (g->t < 0.5) return 0;
-    int it = (int)floor((g->t - 0.5) * (2.0 * d->n_t));
-    int im = (int)floor((g->mu - 0.5) * (2.0 * d->n_mu));
-    if (it >= d->n_t) it = d->n_t - 1;
-    if (im >= d->n_mu) im = d->n_mu - 1;
+    int it = half_unit_bin(g->t, d->n_t);
+    int im = half_unit_bin(g->mu, d->n_mu);
     g->ib = ib;
     g->im = im;
     g->it = it;
