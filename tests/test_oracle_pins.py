@@ -329,3 +329,74 @@ def test_paper_units():
     assert abs(2 * math.pi / g["box_len"] - g["k_min"]) < 0.0005
     assert abs(g["box_len"] / g["n_g"] - g["spacing"]) < 0.005
     assert len(O.rings(int(g["n_g"]))[1]) == 38
+
+
+# --------------------------------------------------------------------------
+# Discrete model [B]_d (Sec. III.C: Eqs. mod_bs and rsd_bs at each
+# combination, binned as the estimator)
+# --------------------------------------------------------------------------
+def _discrete_model_numpy(ng, L, edges, nmu, nt, l_max, A, index, f_ng, beta):
+    """[B]_d rebuilt without the oracle's model code: sides K_i from the ring
+    radii and planes, side cosines from Eq. orient's three lines applied to the
+    oracle's orientation p (checked against n_i / K_i), Y_l^m from scipy."""
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    c = O.combos(ng, L, edges, nmu, nt, half_space=False)
+    _, kp, _ = O.rings(ng)
+    kf = 2 * np.pi / L
+    n = c["ints"][:, :3].astype(float)
+    K = kf * np.sqrt(kp[c["ints"][:, 3:]] ** 2 + n ** 2)
+    K1, t, mu, pz, cphi, deg = c["geo"].T
+    deg = deg > 0
+    # Eq. orient, all three lines, from p = (sin th cos phi, sin th sin phi, p_z)
+    px = np.sqrt(np.maximum(0.0, 1 - pz ** 2)) * cphi
+    sm = np.sqrt(np.maximum(0.0, 1 - mu ** 2))
+    m1 = pz
+    m2 = -mu * pz + sm * px
+    m3 = -((1 - t * mu) * pz + t * sm * px) / np.sqrt(1 - 2 * t * mu + t * t)
+    # where the mean radii close a triangle (mu not clamped), Eq. orient gives
+    # back the cosines n_i / K_i of the combination's own sides
+    # back the cosines n_i / K_i of the combination's own sides; where they do
+    # not (mu clamped, or p_y clamped to 0 because the mean radii and planes
+    # admit no unit p), the model takes n_i / K_i as the oracle's reading says
+    direct = n * kf / K
+    closed = np.abs(K[:, 2] - K1 * np.sqrt(1 - 2 * t * mu + t * t)) < 1e-9 * K1
+    consistent = closed & ~deg & (np.abs(cphi) < 1.0)
+    got = np.stack([m1, m2, m3], 1)
+    assert np.abs(got - direct)[consistent].max() < 1e-9
+    assert consistent.mean() > 0.8
+    mui = np.where(consistent[:, None], got, direct)
+    P = A * K ** index
+    Br = 2 * f_ng * (P[:, 0] * P[:, 1] + P[:, 1] * P[:, 2] + P[:, 2] * P[:, 0])
+    Bs = np.prod(1 + beta * mui ** 2, axis=1) * Br
+    nbin = len(edges) - 1
+    nlm = (l_max + 1) * (l_max + 2) // 2
+    num = np.zeros((nbin * nmu * nt, nlm))
+    den = np.zeros_like(num)
+    th = np.arccos(np.clip(pz, -1, 1))
+    ph = np.arccos(np.clip(cphi, -1, 1))
+    for l in range(l_max + 1):
+        for m in range(l + 1):
+            y = sp.sph_harm_y(l, m, th, ph)                 # mean of Y* over p_y = +-: Re Y
+            w = np.where(deg, y.real if m == 0 else 0.0, y.real)
+            a2 = np.abs(y) ** 2
+            j = O.lm_index(l, m)
+            np.add.at(num[:, j], c["bin"], w * Bs * c["ntri"])
+            np.add.at(den[:, j], c["bin"], a2 * c["ntri"])
+    pref = np.array([np.sqrt((2 * l + 1) / (4 * np.pi)) for l in range(l_max + 1) for m in range(l + 1)])
+    with np.errstate(invalid="ignore", divide="ignore"):
+        B = np.where(den > 0, pref * num / den, np.nan)
+    return B.reshape(nbin, nmu, nt, nlm)
+
+
+def test_discrete_model_matches_an_independent_evaluation():
+    ng, L, l_max = 32, 1000.0, 6
+    edges = synth.default_k1_edges(ng, L, 4)
+    A, index, f_ng, beta = 3.0, -2.0, 0.5, 0.8
+    want = _discrete_model_numpy(ng, L, edges, 5, 5, l_max, A, index, f_ng, beta)
+    got = O.discrete_model(ng, L, edges, 5, 5, l_max, A, index, f_ng, beta)
+    fin = np.isfinite(want)
+    assert np.array_equal(fin, np.isfinite(got))
+    scale = np.abs(want[fin]).max()
+    assert np.abs(got[fin] - want[fin]).max() < 1e-10 * scale
