@@ -224,6 +224,41 @@ def _peaks():
         return 1900.0, 6800.0, "fallback"
 
 
+def golden_errors(workload_name, field, out, W):
+    """Per-moment error of this estimate against the FP64 oracle's stored
+    multipoles of the same workload (tests/golden, written by the oracle
+    alone), when the file exists and its field fingerprint matches the
+    benchmark's field (the same seeded recipe: sampled values to float32
+    rounding, sum of squares to 1e-9).  None otherwise."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    try:
+        import golden_io
+    finally:
+        sys.path.pop(0)
+    g = golden_io.load(workload_name)
+    if g is None or int(g["ng"]) != W["ng"] or float(g["box_len"]) != W["box"]:
+        return None
+    flat = field.reshape(-1)
+    pos = torch.from_numpy(np.asarray(g["field_sample_pos"], dtype=np.int64)).to(flat.device)
+    f64 = flat.double()
+    ok, detail = golden_io.field_check(flat[pos].cpu().numpy(), float(f64.sum()), float((f64 * f64).sum()), g)
+    del f64
+    if not ok:
+        return {"field_matches": False, "detail": detail}
+    B = out.cpu().numpy()[0]
+    ref = g["B"]
+    err = golden_io.floored_rel_err(B, ref)
+    raw = golden_io.raw_rel_err(B, ref)
+    labels = golden_io.moment_labels(LMAX)
+    return {"field_matches": True, "oracle": f"FP64 oracle, all {int(g['n_combos'])} ordered combinations "
+                                            f"({float(g['oracle_wall_s']):.0f} s on {g['host']})",
+            "max_err": float(err.max()), "max_err_per_lm": dict(zip(labels, map(float, err))),
+            "median_raw_rel_err_per_lm": dict(zip(labels, map(float, raw))),
+            "metric": "per moment: max over bins of |B - B_oracle| / max(|B_oracle|, 1e-2 max|B_oracle|)",
+            "bins_compared": int(np.isfinite(ref[..., 0]).sum()), "tolerance": 1e-4}
+
+
 # ----------------------------------------------------------------------------
 def oracle_table(W, edges):
     """The oracle's combination table (its own triangle counts, Eq. Ntri2) and its wall time."""
@@ -282,6 +317,8 @@ def run_reference(args):
     from paper_2405_14513_gb300 import synth
     W = WORKLOADS[args.workload]
     cfg, edges = workload(W, args.precision)
+    cfg["precision"] = "fp64: the FP64 CPU oracle (plain definitions on the full N_g^2 plane, every ordered combination)"
+    cfg["split"] = "replicas"
     n_bins = W["nk1"] * W["nmu"] * W["nmu"]
     field64 = synth.make_field(W["ng"], W["box"], 1).astype(np.float32).astype(np.float64)
     vals, walls = [], []
@@ -363,6 +400,8 @@ def run_ours(args):
     fields_per_step = 1 if shares else world
     value = job_rate(plan.n_bins, fields_per_step, ms / 1e3)
     finite = bool(torch.isfinite(out).any().item())
+    populated = int(torch.isfinite(out[0, ..., 0]).sum().item())
+    golden = golden_errors(args.workload, field, out, W) if rank == 0 else None
     fft_check = fft_crosscheck(plan, field, ws, W["box"])
 
     # end to end through the host side: pinned field in, B out, copies timed
@@ -431,6 +470,11 @@ def run_ours(args):
             "gpu_launches": launches, "clocks": clk,
             "stage_ms_per_step": {k: v / args.steps for k, v in st_ms.items()},
             "stage_share": stage_share, "output_finite": finite,
+            "bins": {"grid": int(plan.n_bins), "populated": populated,
+                     "value_counts": "grid bins: every (k1, mu, t) bin of the output, each with 16 moments; "
+                                     "empty bins (NaN) cost nothing",
+                     "value_populated_bins": job_rate(populated, fields_per_step, ms / 1e3)},
+            "vs_oracle": golden,
             "plan": {k: plan.info[k] for k in ("n_combos", "n_pairs", "n_items", "n_levels",
                                                 "triple_products", "dstore_bytes", "workspace_bytes")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -438,6 +482,8 @@ def run_ours(args):
         del ws
         torch.cuda.empty_cache()
         line["cpu_baseline"] = cpu_baseline(W, edges, f64, plan.n_bins)
+        if golden and golden.get("field_matches"):
+            line["cpu_baseline"]["full_run"] = golden["oracle"] + " (the streamed oracle of the same definitions)"
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -488,7 +534,7 @@ def run_batched(args):
     clk = clocks.stop() if clocks else None
     ms = max_over_ranks(t0.elapsed_time(t1) / args.steps, device=dev)
     value = job_rate(nm * plan.n_bins, world, ms / 1e3)
-    status = plan.device_status(stream)
+    status = plan.workspace_status(ws, G, stream)
 
     # the plain single-job form: the same mocks one by one, no graph
     plan1 = api.Plan(ng, W["box"], edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=1)
@@ -632,7 +678,7 @@ def run_serving(args):
     torch.cuda.empty_cache()
     lat1, span1, _ = srv.run(trace, one_by_one=True)
     single = serve.summary(trace, lat1, span1)
-    status = max(p.device_status() for p in srv.plans.values())
+    status = max(srv.status.values(), default=0)
     cfg = {"workload": "served estimator requests: Poisson arrivals 20/s, N_g in {64,128,256,512} "
                        "(weights 0.4/0.3/0.2/0.1, L 1000/500/1000/2000 Mpc/h), runs of 4-30 of 30 default "
                        "k1 bins, (mu,t) step 0.05, l_max in {2,4,6}; seeded trace of 300 requests",
@@ -651,7 +697,37 @@ def run_serving(args):
     return 0
 
 
+def launch_decision(gpus: int, env) -> tuple:
+    """How this process runs for --gpus N: ("run", None) as one rank of an
+    existing launch (or alone for N = 1), ("spawn", None) to start N ranks
+    itself with torch.distributed.run on this node, or ("error", why) when
+    the launch it is part of has another world size."""
+    world = env.get("WORLD_SIZE")
+    if world is None:
+        return ("spawn", None) if gpus > 1 else ("run", None)
+    if int(world) != gpus:
+        return ("error", f"--gpus {gpus} but WORLD_SIZE={world}: launch one rank per GPU")
+    return ("run", None)
+
+
+def rank_command(gpus: int, argv, port: int) -> list:
+    """The torch.distributed.run command line that runs this script as `gpus`
+    ranks of one node (rendezvous on 127.0.0.1:port) with the same arguments."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + list(argv)
+
+
+def spawn_ranks(gpus: int, argv) -> int:
+    """Run this script as `gpus` ranks of one node; returns their exit status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    return subprocess.call(rank_command(gpus, argv, port))
+
+
 def main(argv=None):
+    argv = sys.argv[1:] if argv is None else argv
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -662,12 +738,18 @@ def main(argv=None):
                          "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace; "
                          "m0: the spherical-shell m = 0 estimator against the ring/plane one at 64^3")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--split", default="replicas", choices=["replicas", "shares"],
-                    help="N > 1: replicas (a field per rank, weak scaling; the default) or shares (one "
-                         "field's Step II split over the ranks, one all-reduce; strong scaling)")
+    ap.add_argument("--split", default="shares", choices=["replicas", "shares"],
+                    help="N > 1: shares (one field's Step II split over the ranks, one all-reduce of the "
+                         "output; strong scaling; the default) or replicas (a field per rank, weak scaling)")
     ap.add_argument("--precision", default="mixed_tc", choices=["mixed_tc", "mixed", "fp32", "fp64"],
                     help="mixed_tc: Step II on tcgen05 (the default); mixed: on FP32 CUDA cores")
     args = ap.parse_args(argv)
+    what, why = launch_decision(args.gpus, os.environ)
+    if what == "error":
+        print(json.dumps({"error": why}), flush=True)
+        return 2
+    if what == "spawn":
+        return spawn_ranks(args.gpus, argv)
     if args.impl == "reference":
         return run_reference(args)
     if "mocks" in WORKLOADS[args.workload]:

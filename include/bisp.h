@@ -144,14 +144,20 @@ size_t estimator_workspace_bytes(const bisp_plan *plan, int batch);
  *   B:         DEVICE pointer, [batch][out_doubles] double: per field the
  *              views' blocks (bisp_view_info); with one view
  *              [batch][n_k1][n_mu][n_t][n_lm].
- * Asynchronous: all work is ordered on `stream`.  Calls that share a plan
- * or a workspace must not overlap on the device. */
+ * Asynchronous: all work is ordered on `stream`.  An estimate only reads
+ * the plan's device tables and writes its workspace and B, so estimates of
+ * one plan may overlap on the device (on different streams) when each has
+ * its own workspace and B and stage timing (estimator_set_timing) is off.
+ * Calls that share a workspace must not overlap.  Host calls on one plan
+ * are not thread safe: make them from one thread. */
 int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *workspace,
                        double *B, void *stream);
 
 /* Same estimate from and to HOST memory: copies delta in, runs, copies B out,
- * and returns when B is complete.  The plan allocates (once, on first use)
- * its own device workspace and staging buffers for max_batch fields. */
+ * and returns when B is complete (and its wait status is checked).  The plan
+ * allocates (once, on first use) its own device workspace and staging
+ * buffers for max_batch fields, so calls of this kind on one plan must not
+ * overlap. */
 int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
                             void *stream);
 
@@ -207,12 +213,25 @@ int estimator_graph_launch(bisp_graph *graph, void *stream);
  * be running. */
 void estimator_graph_destroy(bisp_graph *graph);
 
-/* Device-side status of the plan's kernels: synchronises `stream`, then
- * returns BISP_TIMEOUT if a tensor-core block of an earlier estimate gave up
- * a bounded wait (its combinations then hold NaN), else BISP_OK; the status
- * is cleared.  estimator_estimate_host checks it after every call.  (The
- * paper has no counterpart: this reports the library's own wait bounds.) */
-int estimator_device_status(bisp_plan *plan, void *stream);
+/* Device-side status of one estimate: synchronises `stream`, then returns
+ * BISP_TIMEOUT if a tensor-core Step-II block of the last estimate run in
+ * `workspace` gave up a bounded wait for one of its `batch` fields (those
+ * combinations then hold NaN, and so do the bins they enter), else BISP_OK.
+ * The status lives in the workspace (one word per field, cleared at the start
+ * of every estimate and by this call when set), so estimates in different
+ * workspaces report separately.  workspace: the DEVICE pointer given to
+ * estimator_estimate, or NULL for the array of estimator_estimate_static.
+ * estimator_estimate_host checks it after every call.  (The paper has no
+ * counterpart: this reports the library's own wait bounds.) */
+int estimator_workspace_status(const bisp_plan *plan, const void *workspace, int batch, void *stream);
+
+/* Polls after which the tensor-core Step II's waits on its producer, compute
+ * and MMA-issue stages give up (spins >= 1; 0 restores the default, 2^22).
+ * The wait for the block's own MMAs before it frees its tensor memory keeps
+ * the full bound.  A host-side knob for exercising the give-up path (a block
+ * that gives up writes NaN sums and sets the workspace status); it applies
+ * to later estimates of the plan.  (The paper has no counterpart.) */
+int estimator_set_wait_limit(bisp_plan *plan, int spins);
 
 /* Release the plan and everything it owns (NULL is a no-op).  The caller
  * makes sure no work that uses the plan is still running. */
@@ -324,6 +343,14 @@ int estimator_denominator(const bisp_plan *plan, double *den);
  * Returns the number of combinations (even when larger than cap), < 0 on error. */
 int64_t estimator_combo_table(const bisp_plan *plan, int64_t cap, int32_t *ints, int64_t *ntri,
                               int32_t *bin, int32_t *grid);
+
+/* Shape and orientation of each accepted combination, in estimator_combo_table
+ * order (Eqs. shape and orient; Sec. II, the mapping of a combination to
+ * (p, k1, mu, t) through its mean ring radii): geo[k][4] = mu, t, p_z and
+ * cos phi (the azimuth of the line of sight in the triangle's frame; 1 for a
+ * linear triangle).  geo: HOST pointer with room for `cap` rows.  Returns
+ * the number of combinations (even when larger than cap), < 0 on error. */
+int64_t estimator_combo_geometry(const bisp_plan *plan, int64_t cap, double *geo);
 
 /* After estimator_estimate on this workspace: the real parts of the sums
  * S = sum_x D1 D2 D3 of Eq. fftbs (full N_g^2 grid normalisation) of the last

@@ -95,6 +95,8 @@ def load():
         lib.estimator_denominator.restype = C.c_int
         lib.estimator_combo_table.argtypes = [vp, C.c_int64, vp, vp, vp, vp]
         lib.estimator_combo_table.restype = C.c_int64
+        lib.estimator_combo_geometry.argtypes = [vp, C.c_int64, dp]
+        lib.estimator_combo_geometry.restype = C.c_int64
         lib.estimator_combo_sums.argtypes = [vp, vp, dp, vp]
         lib.estimator_combo_sums.restype = C.c_int
         lib.estimator_dfield.argtypes = [vp, vp, C.c_int, C.c_int, C.c_int, dp, vp]
@@ -107,8 +109,10 @@ def load():
         lib.estimator_graph_launch.restype = C.c_int
         lib.estimator_graph_destroy.argtypes = [vp]
         lib.estimator_graph_destroy.restype = None
-        lib.estimator_device_status.argtypes = [vp, vp]
-        lib.estimator_device_status.restype = C.c_int
+        lib.estimator_workspace_status.argtypes = [vp, vp, C.c_int, vp]
+        lib.estimator_workspace_status.restype = C.c_int
+        lib.estimator_set_wait_limit.argtypes = [vp, C.c_int]
+        lib.estimator_set_wait_limit.restype = C.c_int
         lib.estimator_set_timing.argtypes = [vp, C.c_int]
         lib.estimator_set_timing.restype = C.c_int
         lib.estimator_stage_times.argtypes = [vp, dp, vp]
@@ -324,10 +328,26 @@ class Plan:
             raise BispError(6, "estimator_combo_table", "count mismatch")
         return {"ints": ints[:n], "ntri": ntri[:n], "bin": binv[:n], "grid": grid[:n]}
 
-    def device_status(self, stream=None) -> int:
-        """Synchronise the stream; BISP status of the plan's kernels since the
-        last query (5 = a bounded tensor-core wait gave up), then cleared."""
-        return int(load().estimator_device_status(self._h, _stream_handle(stream)))
+    def combo_geometry(self) -> np.ndarray:
+        """[n_combos][4]: mu, t, p_z, cos phi of each combination (combo_table order)."""
+        n = self.n_combos
+        geo = np.zeros((max(n, 1), 4))
+        got = load().estimator_combo_geometry(self._h, n, _dp(geo))
+        if got != n:
+            raise BispError(6, "estimator_combo_geometry", "count mismatch")
+        return geo[:n]
+
+    def workspace_status(self, workspace=None, batch: int = 1, stream=None) -> int:
+        """Status code of the last estimate run in `workspace` (None: the
+        array of estimator_estimate_static): BISP_TIMEOUT (5) if a
+        tensor-core Step-II block gave up a bounded wait for one of its
+        `batch` fields, else 0.  Synchronises the stream; clears the status."""
+        ws = C.c_void_p(None) if workspace is None else C.c_void_p(workspace.data_ptr())
+        return int(load().estimator_workspace_status(self._h, ws, int(batch), _stream_handle(stream)))
+
+    def set_wait_limit(self, spins: int):
+        """Polls after which the tensor-core Step II's waits give up (0: default)."""
+        _check(load().estimator_set_wait_limit(self._h, int(spins)), "estimator_set_wait_limit")
 
     def combo_sums(self, workspace, stream=None) -> np.ndarray:
         S = np.zeros(max(self.n_combos, 1))

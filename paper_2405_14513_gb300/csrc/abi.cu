@@ -71,7 +71,6 @@ struct bisp_plan {
     TcRow *d_tc_rows = nullptr;
     int32_t *d_tc_slots = nullptr;
     TcUnit *d_tc_units = nullptr;
-    int *d_status = nullptr;             // set by a kernel whose bounded wait ran out
     int64_t *d_doff = nullptr;
     Record *d_rec = nullptr;
     int64_t *d_bin_start = nullptr;
@@ -85,7 +84,11 @@ struct bisp_plan {
     std::vector<int64_t *> d_job_off;    // per level: output offsets of the jobs
     // one field's workspace region (offsets within it); field f of a batch
     // uses bytes [f region_bytes, (f + 1) region_bytes) of the workspace
-    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, region_bytes = 0;
+    // off_status: one int, set by a Step-II block of this field whose bounded
+    // wait ran out; cleared at the start of every estimate
+    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, off_status = 0, region_bytes = 0;
+    int wait_spins = kDefaultWaitSpins;  // bound of the tensor-core Step II's abortable waits
+    int device = -1;                     // the device the plan's tables live on
     int last_field = 0;                  // field of the last estimate that introspection reads
     // transform rows per block picked by the plan's autotuner (0 = default rule)
     int rt_z = 0, rt_xy = 0;
@@ -102,6 +105,9 @@ struct bisp_plan {
     double stage_ms[BISP_N_STAGES] = {};
     int64_t stage_launches[BISP_N_STAGES] = {};
 };
+
+// The device of a plan, for the static-scratch entry point (noalloc.cu).
+int bisp::plan_device(const bisp_plan *p) { return p ? p->device : -1; }
 
 namespace {
 
@@ -539,7 +545,6 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     if (!st) st = upload(p, &p->d_tc_rows, P.tc_rows, s);
     if (!st) st = upload(p, &p->d_tc_slots, P.tc_slots, s);
     if (!st) st = upload(p, &p->d_tc_units, P.tc_units, s);
-    if (!st) st = upload(p, &p->d_status, std::vector<int>(1, 0), s);
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
     if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
@@ -597,6 +602,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->off_dstore = o; o = align256(o + size_t(P.dstore_elems) * p->celem);
     p->off_part = o; o = align256(o + size_t(P.n_partials) * sizeof(double));
     p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
+    p->off_status = o; o = align256(o + sizeof(int));
     p->region_bytes = o;
     CK(cudaStreamSynchronize(s));
     return desc->precision == BISP_PREC_FP64 ? autotune_transforms<double>(p, s) : autotune_transforms<float>(p, s);
@@ -631,12 +637,14 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
     const int64_t fs = int64_t(p->region_bytes);          // between the fields' workspace regions
     StepIIArgs a2{p->d_groups, p->d_tiles, p->d_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk, part, fs};
     TcArgs atc{p->d_tc_tiles, p->d_tc_rows, p->d_tc_slots, p->d_tc_units, p->d_doff, Rg.nz + 1, Rg.nr, p->x_chunk,
-               part, p->d_status, fs};
+               part, reinterpret_cast<int *>(ws + p->off_status), fs, p->wait_spins};
     // every stage runs once for all fields of the batch (gridDim.y = field)
     const unsigned nf = unsigned(batch);
     const Batch in_field{nf, int64_t(ng2) * ng * int64_t(sizeof(R)), fs};   // input field -> region
     const Batch region{nf, fs, fs};
     const Batch to_out{nf, fs, P.n_out * int64_t(sizeof(double))};
+    // the wait status of each field starts clear
+    CK(cudaMemset2DAsync(ws + p->off_status, size_t(fs), 0, sizeof(int), nf, s));
     {   // forward transform: z (real, planes 0..N_g/3 kept) -> y -> x, scaled by V/N_g^3, Delta(0) = 0
         StageMark m(p, BISP_STAGE_FORWARD, 3, s);
         CK(launch_fft_z_real<R>(delta, A_, ng, ng2, Rg.nz + 1, tw, in_field, s, p->rt_z));
@@ -725,6 +733,7 @@ int estimator_plan(bisp_plan **out, const bisp_desc *desc, void *stream)
     bisp_plan *p = nullptr;
     try {
         p = new bisp_plan();
+        if (cudaGetDevice(&p->device) != cudaSuccess) p->device = -1;
         st = build_plan(p, desc, static_cast<cudaStream_t>(stream));
     } catch (const std::bad_alloc &) {
         st = fail(BISP_OUT_OF_MEMORY, "host allocation failed while planning");
@@ -836,7 +845,7 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
     int st = dispatch_estimate(p, p->own_in, batch, p->own_ws, p->own_out, s);
     if (st) return st;
     CK(cudaMemcpyAsync(B_host, p->own_out, outb * batch, cudaMemcpyDeviceToHost, s));
-    return estimator_device_status(p, stream);
+    return estimator_workspace_status(p, p->own_ws, batch, stream);
 }
 
 }  // extern "C"
@@ -908,17 +917,37 @@ void estimator_graph_destroy(bisp_graph *g)
     delete g;
 }
 
-int estimator_device_status(bisp_plan *p, void *stream)
+int estimator_workspace_status(const bisp_plan *p, const void *workspace, int batch, void *stream)
 {
     if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    const unsigned char *ws = static_cast<const unsigned char *>(workspace);
+    if (!ws) {
+        void *a = nullptr;
+        const int st = static_scratch_address(&a);
+        if (st) return st;
+        ws = static_cast<const unsigned char *>(a);
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int h = 0;
-    CK(cudaMemcpyAsync(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    std::vector<int> h(size_t(batch), 0);
+    CK(cudaMemcpy2DAsync(h.data(), sizeof(int), ws + p->off_status, p->region_bytes, sizeof(int), size_t(batch),
+                         cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h == 0) return BISP_OK;
-    CK(cudaMemsetAsync(p->d_status, 0, sizeof(int), s));
+    int bad = 0;
+    for (int v : h) bad |= v != 0;
+    if (!bad) return BISP_OK;
+    CK(cudaMemset2DAsync(const_cast<unsigned char *>(ws) + p->off_status, p->region_bytes, 0, sizeof(int),
+                         size_t(batch), s));
     CK(cudaStreamSynchronize(s));
     return fail(BISP_TIMEOUT, "a tensor-core Step-II block gave up a bounded wait; its sums are NaN");
+}
+
+int estimator_set_wait_limit(bisp_plan *p, int spins)
+{
+    if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    if (spins < 0) return fail(BISP_INVALID_ARG, "negative wait limit");
+    p->wait_spins = spins == 0 ? kDefaultWaitSpins : spins;
+    return BISP_OK;
 }
 
 void estimator_destroy(bisp_plan *p) { free_plan(p); }
@@ -1013,6 +1042,13 @@ int64_t estimator_combo_table(const bisp_plan *p, int64_t cap, int32_t *ints, in
             }
         }
     return P.n_combos;
+}
+
+int64_t estimator_combo_geometry(const bisp_plan *p, int64_t cap, double *geo)
+{
+    if (!p) return -1;
+    if (geo) combo_shapes(p->hp, cap, geo);
+    return p->hp.n_combos;
 }
 
 int estimator_combo_sums(const bisp_plan *p, const void *workspace, double *S, void *stream)

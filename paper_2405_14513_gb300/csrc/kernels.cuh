@@ -114,9 +114,19 @@ struct TcArgs {
     int nz1, nr;
     int64_t x_chunk;
     double *partials;
-    int *status;             // set to 1 by a block whose tensor-core wait ran out
+    int *status;             // field 0's status word, set to 1 by a block whose wait ran out
     int64_t fs;              // bytes between the workspace regions of the fields of a batch
+    int wait_spins;          // polls before an abortable wait gives up
 };
+
+// Polls of an mbarrier before a tensor-core Step-II wait gives up (the plan's
+// default; estimator_set_wait_limit lowers it to test the give-up path).
+constexpr int kDefaultWaitSpins = 1 << 22;
+
+// Device address of estimator_estimate_static's scratch array on the current
+// device (noalloc.cu), and the device a plan lives on (abi.cu).
+int static_scratch_address(void **out);
+int plan_device(const bisp_plan *p);
 
 // One launch per column class: units [lo[c], hi[c]), one block per unit
 // with kTcSmem bytes of shared memory.

@@ -15,10 +15,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include "bisp.h"
+#include "kernels.cuh"
 
 namespace bisp {
 int record_error(int code, const char *msg);
@@ -27,39 +27,32 @@ int record_error(int code, const char *msg);
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB
-constexpr int kMaxDevices = 128;
 
 // The workspace of estimator_estimate_static.  In host code its name is only
 // a stand-in for the device symbol: its device address is looked up with
-// cudaGetSymbolAddress (once per device) and passed to the kernels.
+// cudaGetSymbolAddress, on the device that is current, and passed to the
+// kernels.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_static_scratch on the current device, looked up on the
-// first call for that device.
-int scratch_address(void **out)
+int cuda_fail(const char *what, cudaError_t e)
 {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return bisp::record_error(BISP_CUDA_ERROR, (std::string("cudaGetDevice: ") + cudaGetErrorString(e)).c_str());
-    if (dev < 0 || dev >= kMaxDevices) return bisp::record_error(BISP_INVALID_ARG, "device ordinal out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || !p)
-            return bisp::record_error(BISP_CUDA_ERROR,
-                                      (std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)).c_str());
-        g_scratch_ptr[dev] = p;
-    }
-    *out = g_scratch_ptr[dev];
-    return BISP_OK;
+    return bisp::record_error(BISP_CUDA_ERROR, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
 }
 
 }  // namespace
+
+// Device address of g_static_scratch on the current device.  Looked up on
+// every call (cheap once the module is loaded), so nothing stale survives a
+// cudaDeviceReset; the first lookup on a device loads the library's module
+// there.
+int bisp::static_scratch_address(void **out)
+{
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail("cudaGetSymbolAddress", e);
+    *out = p;
+    return BISP_OK;
+}
 
 extern "C" size_t estimator_static_scratch_bytes(void) { return kStaticScratchBytes; }
 
@@ -74,10 +67,20 @@ extern "C" int estimator_estimate_static(bisp_plan *plan, const void *delta, int
                           " (use estimator_estimate with a caller workspace)";
         return bisp::record_error(BISP_INVALID_ARG, msg.c_str());
     }
+    // the array used is the current device's: the plan and the stream must
+    // belong to that device too
+    int dev = -1, sdev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e);
+    e = cudaStreamGetDevice(static_cast<cudaStream_t>(stream), &sdev);
+    if (e != cudaSuccess) return cuda_fail("cudaStreamGetDevice", e);
+    if (sdev != dev || bisp::plan_device(plan) != dev)
+        return bisp::record_error(BISP_INVALID_ARG, "the plan, the stream and the current device differ");
     void *scratch = nullptr;
-    int st = scratch_address(&scratch);
+    const int st = bisp::static_scratch_address(&scratch);
     if (st) return st;
-    // every workspace element the estimate reads is written earlier in the same
-    // call, so nothing in the scratch has to start at zero
+    // every workspace element the estimate reads is written earlier in the
+    // same call (the wait status too: it is cleared first), so nothing in the
+    // scratch has to start at zero
     return estimator_estimate(plan, delta, batch, scratch, B, stream);
 }

@@ -69,6 +69,57 @@ int triple_level(const Rings &R, int r1, int r2, int r3)
     return R.ngrid - 1;
 }
 
+// Bin of x among n uniform bins of [1/2, 1] with the top edge closed: the
+// number of interior edges 1/2 + j/(2n), j = 1 .. n - 1, lying at or below x
+// (binary search over the edges).
+int half_unit_bin(double x, int n)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int j = (lo + hi + 1) / 2;
+        if (0.5 + double(j) / (2.0 * double(n)) <= x) lo = j;
+        else hi = j - 1;
+    }
+    return lo;
+}
+
+// (k1, mu, t) bin of a shape on an n_mu x n_t grid of [1/2, 1]^2
+int grid_bin(int ib, double mu, double t, int n_mu, int n_t)
+{
+    return (ib * n_mu + half_unit_bin(mu, n_mu)) * n_t + half_unit_bin(t, n_t);
+}
+
+// k1 bin of K1: the last edge at or below K1 (the top edge belongs to the
+// last bin), -1 outside the edges
+static int k1_bin(const std::vector<double> &edges, double K1)
+{
+    const int n = int(edges.size()) - 1;
+    if (!(K1 >= edges[0]) || K1 > edges[n]) return -1;
+    const int b = int(std::upper_bound(edges.begin(), edges.end(), K1) - edges.begin()) - 1;
+    return b < n ? b : n - 1;
+}
+
+bool triangle_shape(const std::vector<double> &k1_edges, double kf, int n_mu, int n_t, double q1, double q2,
+                    double q3, TriShape *s)
+{
+    if (!(q3 > 0.0 && q2 >= q3 && q1 >= q2)) return false;
+    const double a1 = std::sqrt(q1), a2 = std::sqrt(q2), a3 = std::sqrt(q3);
+    const int ib = k1_bin(k1_edges, kf * a1);
+    if (ib < 0) return false;
+    const double t = a2 / a1;
+    if (t < 0.5) return false;
+    double h = (a3 - a1 + a2) * (a3 + a1 - a2) / (2.0 * a1 * a2);
+    h = std::min(0.5, std::max(0.0, h));
+    s->a1 = a1;
+    s->a2 = a2;
+    s->h = h;
+    s->mu = 1.0 - h;
+    s->t = t;
+    s->ib = ib;
+    s->bin = grid_bin(ib, s->mu, t, n_mu, n_t);
+    return true;
+}
+
 namespace {
 
 struct Geo {
@@ -79,58 +130,39 @@ struct Geo {
     double mu, t;              // shape (mu clamped to [1/2, 1])
 };
 
-// (k1, mu, t) bin of a shape on an n_mu x n_t grid of [1/2, 1]^2 (top edges closed)
-int grid_bin(int ib, double mu, double t, int n_mu, int n_t)
-{
-    int it = int(std::floor((t - 0.5) * (2.0 * n_t)));
-    int im = int(std::floor((mu - 0.5) * (2.0 * n_mu)));
-    if (it >= n_t) it = n_t - 1;
-    if (im >= n_mu) im = n_mu - 1;
-    return (ib * n_mu + im) * n_t + it;
-}
-
-// Acceptance and geometry of one combination (planes n1, n2, n3 with ring
-// radii kp1..kp3 in grid units): K1 >= K2 >= K3 > 0 with
-// K_i^2 = k_perp,i^2 + n_i^2; K1 in a k1 bin; t = K2/K1 >= 1/2;
-// mu = (K1^2 + K2^2 - K3^2) / (2 K1 K2) clamped to [1/2, 1];
-// p_z = mu_1, p_x = (mu_2 + mu mu_1)/sqrt(1 - mu^2) (inverse of Eq. orient),
-// p_y = +sqrt(max(0, 1 - p_z^2 - p_x^2)), cos phi = p_x / |(p_x, p_y)|.
+// Acceptance and geometry of one combination (planes n1, n2, n3, ring
+// radii kp1..kp3; grid units), from the triangle it describes: sides
+// a_i^2 = kp_i^2 + n_i^2, shape and bin by triangle_shape.  Orientation, in
+// the frame of Eq. orient (e_z along k1, k2 in the (x, z) plane with x > 0):
+//   k1 = a1 e_z,  k2 = a2 (-mu e_z + s e_x),  k3 = -k1 - k2,
+// s = sqrt(1 - mu^2) = sqrt(h (2 - h)) with h = 1 - mu; the line of sight p
+// obeys k_i . p = n_i (the plane index is the component along the line of
+// sight).  Side 1 gives p_z = n1/a1 and side 3 p_x = ((a2 mu - a1) p_z - n3)
+// / (a2 s) (side 2 then holds by closure); |p| = 1 gives
+// p_y = +sqrt(max(0, 1 - p_z^2 - p_x^2)), and the azimuth cos phi =
+// p_x / sqrt(1 - p_z^2), within [-1, 1] (1 where p_z = +-1: there the
+// azimuth is undefined and P_l^m(p_z) = 0 for m > 0).  A linear triangle
+// (mu >= 1 - 1e-12) is flagged `degenerate`: its azimuth is undefined.
 bool combo_geometry(const HostPlan &P, double kp1, double kp2, double kp3, int n1, int n2, int n3,
                     Geo *g)
 {
     const bisp_desc &d = P.desc;
-    double k1sq = kp1 * kp1 + double(n1) * n1;
-    double k2sq = kp2 * kp2 + double(n2) * n2;
-    double k3sq = kp3 * kp3 + double(n3) * n3;
-    if (!(k1sq >= k2sq && k2sq >= k3sq && k3sq > 0.0)) return false;
-    double s1 = std::sqrt(k1sq), s2 = std::sqrt(k2sq);
-    double K1 = P.kf * s1;
-    int ib = -1;
-    for (int b = 0; b < d.n_k1; ++b)
-        if (P.k1_edges[b] <= K1 && K1 < P.k1_edges[b + 1]) { ib = b; break; }
-    if (ib < 0 && K1 == P.k1_edges[d.n_k1]) ib = d.n_k1 - 1;
-    if (ib < 0) return false;
-    double t = s2 / s1;
-    double mu = (k1sq + k2sq - k3sq) / (2.0 * std::sqrt(k1sq * k2sq));
-    if (mu > 1.0) mu = 1.0;
-    if (mu < 0.5) mu = 0.5;
-    if (t < 0.5) return false;
-    g->bin = grid_bin(ib, mu, t, d.n_mu, d.n_t);
-    g->ib = ib;
-    g->mu = mu;
-    g->t = t;
-    double mu1 = double(n1) / s1;
-    double mu2 = double(n2) / s2;
-    g->pz = mu1;
-    g->degenerate = (mu >= 1.0 - 1e-12);
-    if (g->degenerate) {
-        g->cphi = 1.0;
-    } else {
-        double px = (mu2 + mu * mu1) / std::sqrt(1.0 - mu * mu);
-        double q = 1.0 - g->pz * g->pz - px * px;
-        double py = std::sqrt(q > 0.0 ? q : 0.0);
-        double rho = std::sqrt(px * px + py * py);
-        g->cphi = rho > 0.0 ? px / rho : 1.0;
+    TriShape sh;
+    if (!triangle_shape(P.k1_edges, P.kf, d.n_mu, d.n_t, kp1 * kp1 + double(n1) * n1,
+                        kp2 * kp2 + double(n2) * n2, kp3 * kp3 + double(n3) * n3, &sh))
+        return false;
+    g->ib = sh.ib;
+    g->mu = sh.mu;
+    g->t = sh.t;
+    g->bin = sh.bin;
+    g->pz = double(n1) / sh.a1;
+    g->degenerate = (sh.mu >= 1.0 - 1e-12);
+    g->cphi = 1.0;
+    if (!g->degenerate) {
+        const double sperp = std::sqrt(sh.h * (2.0 - sh.h));
+        const double px = ((sh.a2 * sh.mu - sh.a1) * g->pz - double(n3)) / (sh.a2 * sperp);
+        const double rho2 = 1.0 - g->pz * g->pz;
+        if (rho2 > 0.0) g->cphi = std::min(1.0, std::max(-1.0, px / std::sqrt(rho2)));
     }
     return true;
 }
@@ -687,6 +719,25 @@ void build_views(HostPlan &P, const int *n_mu_l, const int *n_t_l)
         bs += v.n_bins + 1;
     }
     P.n_out = off;
+}
+
+void combo_shapes(const HostPlan &P, int64_t cap, double *out)
+{
+    const Rings &R = P.rings;
+    for (const auto &G : P.groups)
+        for (int s = 0; s < G.nrow; ++s) {
+            const Row &rw = P.rows[G.row0 + s];
+            for (int j = 0; j < rw.n; ++j) {
+                const int64_t k = G.c0 + rw.coff + j;
+                if (k >= cap) continue;
+                Geo g;
+                combo_geometry(P, R.kperp[rw.r1], R.kperp[rw.r2], R.kperp[rw.r3a + j], G.n1, G.n2, G.n3, &g);
+                out[4 * k] = g.mu;
+                out[4 * k + 1] = g.t;
+                out[4 * k + 2] = g.pz;
+                out[4 * k + 3] = g.cphi;
+            }
+        }
 }
 
 void sort_records(HostPlan &P)

@@ -252,7 +252,26 @@ std::string enumerate(HostPlan &P, int64_t x_chunk);
 void build_views(HostPlan &P, const int *n_mu_l, const int *n_t_l);
 
 // Counting sort of the records by (k1, mu, t) bin, once per view.
+// Shape of a triangle with squared sides q1 >= q2 >= q3 > 0 (grid units)
+// and its (k1, mu, t) bin (Eq. shape; Sec. II, second-level binning): side
+// lengths a_i = sqrt(q_i); accepted when K1 = kf a1 lies in a k1 bin and
+// t = a2/a1 >= 1/2.  mu = -k1^.k2^ is the cosine of the triangle's angle
+// between k1 and -k2 (opposite side 3), from the half-angle form of the
+// cosine law, 1 - mu = 2 sin^2(gamma/2) = (a3 - a1 + a2)(a3 + a1 - a2) /
+// (2 a1 a2), clamped to [1/2, 1] (where it lies for a1 >= a2 >= a3).
+struct TriShape {
+    double a1, a2, h, mu, t;   // h = 1 - mu
+    int ib, bin;
+};
+bool triangle_shape(const std::vector<double> &k1_edges, double kf, int n_mu, int n_t, double q1, double q2,
+                    double q3, TriShape *s);
+// bin of x among n uniform bins of [1/2, 1] (top edge closed) and the flat
+// (k1, mu, t) bin on an n_mu x n_t grid
+int half_unit_bin(double x, int n);
+int grid_bin(int ib, double mu, double t, int n_mu, int n_t);
 void sort_records(HostPlan &P);
+// mu, t, p_z, cos phi of every combination, in S order: out[4 k + 0..3]
+void combo_shapes(const HostPlan &P, int64_t cap, double *out);
 
 // Step-II block classes of the plan's kernel (tcgen05: NC = 16, 32, 48, 64;
 // CUDA cores: 2^c warps, c = 2, 3, 4), as ranges of its launch-ordered units.

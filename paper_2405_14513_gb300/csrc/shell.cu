@@ -227,30 +227,16 @@ cudaError_t fft3(typename Cx<R>::T *a, typename Cx<R>::T *b, int ng, int64_t nb,
     return e;
 }
 
-// the acceptance and (k1, mu, t) bin of a shell triple, the same IEEE
-// operations as a ring combination with n1 = n2 = n3 = 0
+// the acceptance and (k1, mu, t) bin of a shell triple: the triangle of
+// sides K1, K2, K3 (mean shell radii, grid units) shaped and binned like a
+// ring combination with n1 = n2 = n3 = 0
 bool triple_bin(const bisp_shell_plan &P, double kp1, double kp2, double kp3, int *bin)
 {
     const bisp_desc &d = P.desc;
-    const double k1sq = kp1 * kp1 + 0.0, k2sq = kp2 * kp2 + 0.0, k3sq = kp3 * kp3 + 0.0;
-    if (!(k1sq >= k2sq && k2sq >= k3sq && k3sq > 0.0)) return false;
-    const double s1 = std::sqrt(k1sq), s2 = std::sqrt(k2sq);
-    const double K1 = (kShellTwoPi / d.box_len) * s1;
-    int ib = -1;
-    for (int b = 0; b < d.n_k1; ++b)
-        if (P.edges[b] <= K1 && K1 < P.edges[b + 1]) { ib = b; break; }
-    if (ib < 0 && K1 == P.edges[d.n_k1]) ib = d.n_k1 - 1;
-    if (ib < 0) return false;
-    const double t = s2 / s1;
-    double mu = (k1sq + k2sq - k3sq) / (2.0 * std::sqrt(k1sq * k2sq));
-    if (mu > 1.0) mu = 1.0;
-    if (mu < 0.5) mu = 0.5;
-    if (t < 0.5) return false;
-    int it = int(std::floor((t - 0.5) * (2.0 * d.n_t)));
-    int im = int(std::floor((mu - 0.5) * (2.0 * d.n_mu)));
-    if (it >= d.n_t) it = d.n_t - 1;
-    if (im >= d.n_mu) im = d.n_mu - 1;
-    *bin = (ib * d.n_mu + im) * d.n_t + it;
+    TriShape sh;
+    if (!triangle_shape(P.edges, kShellTwoPi / d.box_len, d.n_mu, d.n_t, kp1 * kp1, kp2 * kp2, kp3 * kp3, &sh))
+        return false;
+    *bin = sh.bin;
     return true;
 }
 

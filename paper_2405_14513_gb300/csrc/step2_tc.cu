@@ -38,7 +38,7 @@ namespace {
 constexpr int kTX = kTcTX;                   // grid points per stage (K = 32)
 constexpr int kSlotBytes = kTcSlotBytes;
 constexpr uint32_t kTmemCols = 256;          // A[2] (hi 32 + lo 32 columns each), then the accumulators
-constexpr int kWaitSpins = 1 << 22;          // bound of a tensor-core completion wait
+constexpr int kDrainSpins = kDefaultWaitSpins;  // bound of the wait for the block's own MMAs
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -169,11 +169,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m)
 }
 
 // Bounded wait for phase `parity` of m; gives up (false) when the block is
-// aborting or after kWaitSpins polls, and then raises the abort flag.
-__device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, volatile int *abort)
+// aborting or after `spins` polls, and then raises the abort flag.
+__device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, volatile int *abort, int spins)
 {
     const uint32_t a = su32(m);
-    for (int i = 0; i < kWaitSpins; ++i) {
+    for (int i = 0; i < spins; ++i) {
         uint32_t ok;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(ok) : "r"(a), "r"(parity) : "memory");
@@ -185,11 +185,11 @@ __device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, vo
 }
 
 // Bounded wait for phase `parity` of m that does not stop at the abort flag
-// (waits for the block's own tensor-core work).
+// (waits for the block's own tensor-core work; always the full bound).
 __device__ __forceinline__ void mbar_wait_bounded(uint64_t *m, uint32_t parity)
 {
     const uint32_t a = su32(m);
-    for (int i = 0; i < kWaitSpins; ++i) {
+    for (int i = 0; i < kDrainSpins; ++i) {
         uint32_t ok;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(ok) : "r"(a), "r"(parity) : "memory");
@@ -255,6 +255,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     // field blockIdx.y of a batch: its D store and partial sums
     dstore = reinterpret_cast<const float2 *>(reinterpret_cast<const char *>(dstore) + int64_t(blockIdx.y) * args.fs);
     args.partials = reinterpret_cast<double *>(reinterpret_cast<char *>(args.partials) + int64_t(blockIdx.y) * args.fs);
+    args.status = reinterpret_cast<int *>(reinterpret_cast<char *>(args.status) + int64_t(blockIdx.y) * args.fs);
+    const int spins = args.wait_spins;
     const int nslot = T.nslot, nf = nslot + NC;
     const int S = tc_stages(NC, nslot);          // ring depth (>= 3; the plan checked)
     const int rowb = (nf + 1) * kSlotBytes;      // one ring buffer: nf fields and a zero row
@@ -332,7 +334,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         int q = 0;                                   // ring buffer of stage st
         uint32_t ph = 0;                             // its phase: (st / S) & 1
         for (int st = 0; st < nstage && ok; ++st) {
-            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], ph ^ 1u, abort);
+            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], ph ^ 1u, abort, spins);
             if (!ok) break;
             const float2 *src = dstore + x0 + int64_t(st) * kTX + 2 * p;
             const uint32_t dst = su32(sS + q * rowb + f0 * kSlotBytes + p * 16);
@@ -350,8 +352,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
             for (int st = 0; st < nstage && ok; ++st) {
                 const int b = st & 1;
-                ok = mbar_wait_abort(&sy->aready[b], uint32_t(st >> 1) & 1, abort);
-                if (ok && st >= 2) ok = mbar_wait_abort(&sy->dfree[b], uint32_t((st - 2) >> 1) & 1, abort);
+                ok = mbar_wait_abort(&sy->aready[b], uint32_t(st >> 1) & 1, abort, spins);
+                if (ok && st >= 2) ok = mbar_wait_abort(&sy->dfree[b], uint32_t((st - 2) >> 1) & 1, abort, spins);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a = tmem + 64 * b;
@@ -392,7 +394,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         for (int st = 0; st <= nstage && ok; ++st) {
             if (st < nstage) {
                 const int b = st & 1;
-                ok = mbar_wait_abort(&sy->full[q], ph, abort);
+                ok = mbar_wait_abort(&sy->full[q], ph, abort, spins);
                 if (!ok) break;
                 const unsigned char *sq = sS + q * rowb;
                 const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
@@ -429,7 +431,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 // accumulators of stage st - 1 (buffer b)
                 const int b = (st - 1) & 1;
                 const uint32_t par = uint32_t((st - 1) >> 1) & 1;
-                ok = mbar_wait_abort(&sy->mdone[b], par, abort);
+                ok = mbar_wait_abort(&sy->mdone[b], par, abort, spins);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 add_accumulator<NH>(tlane + 128 + 64 * b + NH * half, acc);

@@ -13,6 +13,11 @@ workspace) taken from a pool bounded by the HBM budget.  Launches on
 different streams overlap on the GPU; requests that arrive meanwhile join
 the next batch of their size.
 
+Launches of one plan run at the same time on different streams; the C ABI
+allows that because each slot has its own workspace and output (an estimate
+only reads the plan's tables), and each launch's wait status is read from its
+own workspace, so a request is told of a failure in its own launch only.
+
 `Scheduler` holds the decisions and nothing of the GPU (tested on the CPU);
 `Server` runs them on the device.
 """
@@ -202,12 +207,14 @@ class Server:
         """Serve the trace in real time (arrival times from its start).
         one_by_one: a single stream, one request per launch, no overlap (the
         plain single-job form).  Returns per-request latencies (s), the
-        makespan (s), and the results when asked."""
+        makespan (s), and the results when asked.  self.status[rid] is the
+        status code of the launch that served request rid (0: success)."""
         torch = self.torch
         sched = self.sched
         if one_by_one:
             sched = Scheduler({ng: 1 for ng in self.grids}, self.sched.slot_bytes, self.sched.budget, 1)
         lat, res = {}, {}
+        self.status = {}
         self.log = []           # (N_g, fields) of every launch
         pending = []            # (event, slot, batch, stream index)
         free_streams = list(range(len(self.streams) if not one_by_one else 1))
@@ -223,8 +230,10 @@ class Server:
                 if ev.query():
                     t_done = time.perf_counter() - t0
                     out = slot.handle["out"]
+                    st = self.plans[slot.ng].workspace_status(slot.handle["ws"], len(batch), self.streams[si])
                     for j, r in enumerate(batch):
                         lat[r.rid] = t_done - r.t_arrive
+                        self.status[r.rid] = st
                         if keep_results:
                             res[r.rid] = self.answer(r, out[j]).cpu().numpy()
                     sched.done(slot)

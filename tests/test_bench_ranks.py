@@ -51,3 +51,25 @@ def test_single_process_has_no_group():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.job_rate(100, 1, 2.0) == 50.0
+
+
+def test_launch_decision_spawns_or_refuses():
+    """--gpus N without a launcher starts N ranks itself; inside a launch of
+    another size it refuses (exit status 2) instead of running one rank."""
+    import subprocess
+    import sys
+
+    import bench
+    assert bench.launch_decision(1, {}) == ("run", None)
+    assert bench.launch_decision(4, {}) == ("spawn", None)
+    assert bench.launch_decision(4, {"WORLD_SIZE": "4"}) == ("run", None)
+    what, why = bench.launch_decision(8, {"WORLD_SIZE": "1"})
+    assert what == "error" and "WORLD_SIZE=1" in why
+    cmd = bench.rank_command(4, ["--gpus", "4", "--steps", "2"], 29555)
+    assert cmd[1:3] == ["-m", "torch.distributed.run"]
+    assert "--nproc-per-node=4" in cmd and "--master-addr=127.0.0.1" in cmd and "--master-port=29555" in cmd
+    assert cmd[-4:] == ["--gpus", "4", "--steps", "2"] and cmd[-5].endswith("bench.py")
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, bench.__file__, "--gpus", "2"], env=env, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 2 and "WORLD_SIZE=1" in r.stdout

@@ -101,14 +101,42 @@ def test_step1_dfields_on_every_grid(c64):
 
 
 def test_combination_table_matches_oracle(c64):
+    """The product computes each combination's shape, orientation and bin on a
+    route of its own (half-angle cosine law, the line of sight from the
+    closing side, a search over bin edges); the oracle takes the cosine law
+    and inverts Eq. orient.  The same combinations and triangle counts, the
+    same shape and orientation to rounding, and the same bins except where the
+    oracle's mu, t or K1 lies within 1e-12 of a bin edge (counted; at most one
+    bin apart along that axis)."""
     tab = c64.plan.combo_table()
+    geo = c64.plan.combo_geometry()
     ref = O.combos(c64.ng, c64.L, c64.edges, c64.nmu, c64.nt, half_space=True)
     key = lambda ints: [tuple(r) for r in ints]
-    g = dict(zip(key(tab["ints"]), zip(tab["ntri"], tab["bin"])))
-    o = dict(zip(key(ref["ints"]), zip(ref["ntri"], ref["bin"])))
+    g = dict(zip(key(tab["ints"]), range(len(tab["ints"]))))
+    o = dict(zip(key(ref["ints"]), range(len(ref["ints"]))))
     assert set(g) == set(o)
-    for k, v in o.items():
-        assert g[k] == (v[0], v[1]), k
+    gi = np.array([g[k] for k in o])
+    oi = np.array(list(o.values()))
+    assert np.array_equal(tab["ntri"][gi], ref["ntri"][oi])
+    rg, ro = geo[gi], ref["geo"][oi]                  # product: mu, t, pz, cphi; oracle: K1, t, mu, pz, cphi, deg
+    assert np.abs(rg[:, 0] - ro[:, 2]).max() < 1e-13
+    assert np.abs(rg[:, 1] - ro[:, 1]).max() < 1e-15
+    assert np.abs(rg[:, 2] - ro[:, 3]).max() < 1e-15
+    sin_g = np.sqrt(np.maximum(0.0, 1.0 - rg[:, 2] ** 2))
+    sin_o = np.sqrt(np.maximum(0.0, 1.0 - ro[:, 3] ** 2))
+    assert np.abs(sin_g * rg[:, 3] - sin_o * ro[:, 4]).max() < 1e-11
+    # bins: exact away from the edges
+    def near(x, edges):
+        return np.abs(x[:, None] - edges[None, :]).min(axis=1) < 1e-12 * np.maximum(1.0, np.abs(x))
+    mu_e = 0.5 + np.arange(1, c64.nmu) / (2.0 * c64.nmu)
+    t_e = 0.5 + np.arange(1, c64.nt) / (2.0 * c64.nt)
+    edge = near(ro[:, 2], mu_e) | near(ro[:, 1], t_e) | near(ro[:, 0], c64.edges[1:-1])
+    diff = tab["bin"][gi] != ref["bin"][oi]
+    assert not np.any(diff & ~edge)
+    assert diff.sum() <= max(1, 1e-4 * len(diff)), (int(diff.sum()), int(edge.sum()))
+    nb = c64.nmu * c64.nt
+    a, b = tab["bin"][gi][diff], ref["bin"][oi][diff]
+    assert np.all(a // nb == b // nb) and np.all(np.abs(a % nb - b % nb) <= c64.nt)
 
 
 def test_denominators_match_oracle(c64):
@@ -208,7 +236,7 @@ def test_tensor_core_ragged_and_degenerate_configurations():
         if edges is None:
             edges = synth.default_k1_edges(ng, L, 1)
         c = Case(ng, L, len(edges) - 1, nmu, nt, lmax, precision="mixed_tc", edges=edges, seed=7)
-        assert c.plan.device_status() == 0
+        assert c.plan.workspace_status(c.ws, 1) == 0
         ref = O.select_even(c.oracle["B"], lmax)
         if np.isfinite(ref).any():
             assert floored_rel_err(c.B, ref).max() < TOL["mixed_tc"]
@@ -222,7 +250,7 @@ def test_tensor_core_128_sampled_sums_and_cuda_core_agreement():
     CUDA-core FP32 path."""
     ng, L = 128, 500.0
     tc = Case(ng, L, 12, 20, 20, 6, precision="mixed_tc", seed=11)
-    assert tc.plan.device_status() == 0
+    assert tc.plan.workspace_status(tc.ws, 1) == 0
     tab = tc.plan.combo_table()
     S = tc.plan.combo_sums(tc.ws)
     pick = np.random.default_rng(12).choice(len(S), size=300, replace=False)
@@ -244,7 +272,7 @@ def test_tensor_core_full_size_512_sampled():
     fd = synth.make_field_torch(ng, L, 1, device="cuda").float().contiguous()
     field = fd.cpu().numpy()                      # the values the GPU sees, for the oracle
     B = plan.estimate(fd[None], ws).cpu().numpy()[0]
-    assert plan.device_status() == 0
+    assert plan.workspace_status(ws, 1) == 0
     assert np.isfinite(B).any() and not np.isnan(B[np.isfinite(B)]).any()
     tab = plan.combo_table()
     S = plan.combo_sums(ws)
@@ -302,7 +330,7 @@ def test_captured_estimate_replays_exactly():
     g.launch(stream=side)
     side.synchronize()
     assert np.array_equal(out.cpu().numpy(), want2, equal_nan=True)
-    assert plan.device_status() == 0
+    assert plan.workspace_status(ws, fields.shape[0]) == 0
     g.close()
     plan.close()
 
@@ -330,7 +358,7 @@ def test_grid_384_sampled_sums():
     fd = synth.make_field_torch(ng, L, 3, beta=1.0, device="cuda").float().contiguous()
     field = fd.cpu().numpy()
     plan.estimate(fd[None], ws)
-    assert plan.device_status() == 0
+    assert plan.workspace_status(ws, 1) == 0
     tab = plan.combo_table()
     S = plan.combo_sums(ws)
     rng = np.random.default_rng(19)
@@ -452,4 +480,34 @@ def test_mock_statistics_match_per_field_estimates():
     assert np.abs(mean[ok] - ref_mean[ok]).max() <= 1e-12 * scale
     assert np.abs(std[ok] - ref_std[ok]).max() <= 1e-10 * scale
     assert np.isnan(mean[c == 0]).all()
+    plan.close()
+
+
+def test_tensor_core_waits_give_up_and_the_plan_recovers():
+    """The tcgen05 Step II bounds every wait.  With the limit cut to one poll
+    (the producers' first copies cannot have landed by then), its blocks give
+    up: they write NaN sums, and the workspace status reports BISP_TIMEOUT for
+    that estimate only; every populated bin is then NaN.  With the default
+    limit restored, the next estimate on the same plan and workspace is the
+    normal one again, bit for bit, and reports success."""
+    ng, L = 16, 1000.0
+    edges = synth.default_k1_edges(ng, L, 3)
+    field = torch.from_numpy(synth.make_field(ng, L, 2).astype(np.float32)).cuda()[None].contiguous()
+    plan = api.Plan(ng, L, edges, 5, 5, 6, precision="mixed_tc")
+    ws, other = plan.workspace(1), plan.workspace(1)
+    ref = plan.estimate(field, ws).cpu().numpy()
+    assert plan.workspace_status(ws, 1) == 0
+    fin = np.isfinite(ref)
+    assert fin.any()
+    plan.set_wait_limit(1)
+    bad = plan.estimate(field, ws).cpu().numpy()
+    assert plan.workspace_status(ws, 1) == 5                  # BISP_TIMEOUT
+    assert plan.workspace_status(ws, 1) == 0                  # reading it cleared it
+    assert np.isnan(bad[fin]).all()
+    plan.set_wait_limit(0)
+    good = plan.estimate(field, other).cpu().numpy()
+    assert plan.workspace_status(other, 1) == 0
+    again = plan.estimate(field, ws).cpu().numpy()
+    assert plan.workspace_status(ws, 1) == 0
+    assert np.array_equal(again, ref, equal_nan=True) and np.array_equal(good, ref, equal_nan=True)
     plan.close()

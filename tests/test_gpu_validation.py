@@ -37,7 +37,7 @@ def test_mean_over_realisations_matches_discrete_model():
         f = torch.stack([synth.make_field_torch(ng, L, 1 + s, sigma_g=sigma_g, f_ng=f_ng, beta=beta,
                                                 device="cuda").float() for s in range(s0, s0 + batch)])
         out.append(plan.estimate(f.contiguous(), ws).cpu().numpy())
-    assert plan.device_status() == 0
+        assert plan.workspace_status(ws, batch) == 0
     plan.close()
     B = np.concatenate(out)[:, 0]                                   # [seed][mu][t][lm]
     A = synth.power_amplitude(ng, L, sigma_g, -2.0)
