@@ -54,6 +54,9 @@ WORKLOADS = {
     "c5": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 10, "requests": 300, "rate": 20.0},
     # the spherical-shell m = 0 estimator against the ring/plane estimator on c1's workload
     "m0": {"ng": 64, "box": 1000.0, "nk1": 6, "nmu": 5, "shells": True},
+    # the paper's validation (Sec. III.B): 50 realisations at N_g = 384, L = 215 Mpc,
+    # beta = 1, k1 = 2.1 +- 0.1 Mpc^-1, against the stored discrete model [B]_d
+    "val": {"ng": 384, "box": 215.0, "nk1": 1, "nmu": 10, "realisations": 50, "batch": 10},
 }
 SM_COUNT, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 TF32_PER_BF16 = 1.1 / 2.25          # nominal dense tensor rates of GB300
@@ -726,6 +729,84 @@ def spawn_ranks(gpus: int, argv) -> int:
     return subprocess.call(rank_command(gpus, argv, port))
 
 
+def run_validation(args):
+    """The paper's statistical validation (Sec. III.B): the mean over 50
+    seeded realisations against the discrete model [B]_d (stored by the
+    oracle in tests/golden/val384_oracle_B.npz), per moment and bin:
+    Delta = |mean - [B]_d| / sigma, sigma the standard error of the mean over
+    the realisations, and the discreteness weights w = [B]_d / [B]_c the
+    oracle stored beside it.  One step = all realisations."""
+    import torch
+
+    from paper_2405_14513_gb300 import api, synth
+
+    rank, world, local = _dist()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sys.path.insert(0, os.path.join(ROOT, "tests", "golden"))
+    import golden_io
+    sys.path.pop(0)
+    g = golden_io.load("val384")
+    if g is None:
+        print(json.dumps({"error": "tests/golden/val384_oracle_B.npz missing"}), flush=True)
+        return 1
+    W = WORKLOADS["val"]
+    ng, L, nr, G = W["ng"], W["box"], W["realisations"], W["batch"]
+    edges = np.asarray(g["k1_edges"])
+    plan = api.Plan(ng, L, edges, W["nmu"], W["nmu"], LMAX, precision=args.precision, max_batch=G)
+    ws = plan.workspace(G, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    kw = dict(sigma_g=float(g["sigma_g"]), f_ng=float(g["f_ng"]), beta=float(g["beta"]), device=dev)
+    fields = torch.empty((G, ng, ng, ng), dtype=torch.float32, device=dev)
+    B = []
+    status = 0
+    t_est = 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for s0 in range(0, nr, G):
+        for i in range(G):
+            fields[i] = synth.make_field_torch(ng, L, 1 + s0 + i, **kw).float()
+        e0.record(stream)
+        out = plan.estimate(fields, ws, stream=stream)
+        e1.record(stream)
+        status = max(status, plan.workspace_status(ws, G, stream))
+        t_est += e0.elapsed_time(e1)
+        B.append(out.cpu().numpy()[:, 0])                # [field][mu][t][lm]
+    B = np.concatenate(B)
+    mean, sem = B.mean(0), B.std(0, ddof=1) / np.sqrt(nr)
+    Bd = g["B_d"][0]
+    labels = golden_io.moment_labels(LMAX)
+    fin = np.isfinite(Bd[..., 0]) & np.isfinite(mean[..., 0])
+    per = {}
+    for j, lab in enumerate(labels):
+        with np.errstate(invalid="ignore", divide="ignore"):
+            d = np.abs(mean[..., j] - Bd[..., j]) / sem[..., j]
+        dv = d[fin]
+        w = g["w"][0][..., j][fin]
+        per[lab] = {"chi2_per_bin": float(np.mean(dv ** 2)), "frac_le_3": float(np.mean(dv <= 3)),
+                    "n_3_to_5": int(np.sum((dv > 3) & (dv <= 5))), "n_5_to_7": int(np.sum((dv > 5) & (dv <= 7))),
+                    "n_gt_7": int(np.sum(dv > 7)), "max": float(dv.max()),
+                    "delta_map": np.round(np.where(fin, d, np.nan), 2).tolist(),
+                    "w_median_abs_dev_from_1": float(np.nanmedian(np.abs(w - 1))) if np.isfinite(w).any() else None}
+    frac = (mean[..., 0] - Bd[..., 0]) / Bd[..., 0]
+    line = {"metric": "validation: Delta_l^m = |mean - [B]_d| / sigma over 50 realisations (paper Sec. III.B)",
+            "value": float(np.mean([p["frac_le_3"] for p in per.values()])), "unit": "fraction of bins with Delta<=3",
+            "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": t_est, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"N_g={ng}^3, L={L:g} Mpc, P=A k^-2 (sigma_G={float(g['sigma_g'])}), "
+                                   f"f_NG={float(g['f_ng'])}, beta={float(g['beta'])}, k1 in [{edges[0]}, {edges[1]}) "
+                                   f"Mpc^-1, (mu,t) step 0.05, l<=6, {nr} realisations",
+                       "precision": f"{args.precision}: {PRECISION_TEXT[args.precision]}",
+                       "model": "[B]_d of the FP64 oracle (tests/golden/val384_oracle_B.npz)"},
+            "bins": int(fin.sum()), "monopole_fractional_deviation": [float(np.nanmin(frac[fin])),
+                                                                      float(np.nanmax(frac[fin]))],
+            "per_moment": per, "device_status": status}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    return 0
+
+
 def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
@@ -736,7 +817,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS),
                     help="c3: 512^3 headline (default); c2: 256^3, L=1000, 20 k1 bins; c1: 64^3, L=1000, "
                          "6 bins; c4: 256 mocks of 128^3 in batched graphs; c5: served request trace; "
-                         "m0: the spherical-shell m = 0 estimator against the ring/plane one at 64^3")
+                         "m0: the spherical-shell m = 0 estimator against the ring/plane one at 64^3; "
+                         "val: the paper's validation, 50 realisations at 384^3 against [B]_d")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--split", default="shares", choices=["replicas", "shares"],
                     help="N > 1: shares (one field's Step II split over the ranks, one all-reduce of the "
@@ -758,6 +840,8 @@ def main(argv=None):
         return run_serving(args)
     if "shells" in WORKLOADS[args.workload]:
         return run_shells(args)
+    if "realisations" in WORKLOADS[args.workload]:
+        return run_validation(args)
     return run_ours(args)
 
 

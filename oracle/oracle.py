@@ -334,3 +334,33 @@ def shell_estimate(delta, box_len, k1_edges, n_mu, n_t, l_max, direct=False, nth
     if _load().bo_shell_estimate(C.byref(desc), _dp(d_arr), _dp(B)) < 0:
         raise ValueError("invalid estimator parameters")
     return B
+
+
+def discreteness_weights(ng, box_len, k1_edges, n_mu, n_t, l_max, A, index, f_ng, beta, nthreads=0):
+    """Discreteness weights w_l^m = [B_l^m]_d / [B_l^m]_c (Sec. III.C): the
+    discrete model binned as the estimator, over the continuum integral of
+    Eq. bs_lm at each bin's mean triangle (K1, mu, t averaged over the bin's
+    combinations with their triangle counts as weights).  Returns a dict of
+    arrays [n_k1][n_mu][n_t][n_lm_all]: "d", "c" and "w" (NaN for empty bins
+    and where |[B]_c| is below 1e-12 of the bin's monopole), and the mean
+    shape "k1_mu_t" [n_k1][n_mu][n_t][3]."""
+    d = discrete_model(ng, box_len, k1_edges, n_mu, n_t, l_max, A, index, f_ng, beta, nthreads)
+    c = combos(ng, box_len, k1_edges, n_mu, n_t, half_space=False, nthreads=nthreads)
+    nb = d.shape[0] * n_mu * n_t
+    w = c["ntri"].astype(np.float64)
+    wsum = np.bincount(c["bin"], weights=w, minlength=nb)
+    shape = np.full((nb, 3), np.nan)
+    for j, col in enumerate((0, 2, 1)):           # geo: K1, t, mu -> (k1, mu, t)
+        s = np.bincount(c["bin"], weights=w * c["geo"][:, col], minlength=nb)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            shape[:, j] = np.where(wsum > 0, s / wsum, np.nan)
+    cont = np.full((nb, n_moments_all(l_max)), np.nan)
+    for b in range(nb):
+        if wsum[b] > 0:
+            k1, mu, t = shape[b]
+            cont[b] = continuum(A, index, f_ng, beta, k1, mu, t, l_max).real
+    cont = cont.reshape(d.shape)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        big = np.abs(cont) > 1e-12 * np.abs(cont[..., :1])
+        ratio = np.where(big, d / np.where(big, cont, 1.0), np.nan)
+    return {"d": d, "c": cont, "w": ratio, "k1_mu_t": shape.reshape(d.shape[:3] + (3,))}

@@ -7,6 +7,10 @@ Calls only the oracle (``oracle/``) and the seeded input generator
 arithmetic).  The oracle runs in slabs of n1 with a checkpoint after each
 slab (``oracle.estimate_stream``), so an interrupted run resumes.
 
+val384 holds no estimate: the oracle's discrete model [B]_d, the continuum
+[B]_c of Eq. bs_lm at each bin's mean triangle and the discreteness weights
+w = [B]_d / [B]_c for the paper's validation setup (Sec. III.B-C).
+
 Workloads (seeded synthetic field: P = A k^-2, sigma_G = 0.1, f_NG = 0.5,
 Kaiser beta = 0.5, seed 1, cast to float32 as the estimator reads it):
 
@@ -21,7 +25,7 @@ fingerprint of the float32 field: its sha256, its sum and sum of squares in
 float64, and 4096 values at fixed positions.  A test that regenerates the
 field on another host checks the fingerprint before it compares.
 
-  python tests/golden/make_oracle_golden.py c3 [--threads N] [--ckpt PATH]
+  python tests/golden/make_oracle_golden.py c3|c2|val384 [--threads N] [--ckpt PATH]
 """
 from __future__ import annotations
 
@@ -45,6 +49,13 @@ from paper_2405_14513_gb300 import synth            # noqa: E402
 CONFIGS = {
     "c3": {"ng": 512, "box": 2000.0, "nk1": 30, "nmu": 20, "l_max": 6, "seed": 1},
     "c2": {"ng": 256, "box": 1000.0, "nk1": 20, "nmu": 20, "l_max": 6, "seed": 1},
+}
+# the paper's validation setup (Sec. III.B): N_g = 384, L = 215 Mpc, P = A k^-2
+# with sigma_G = 0.1, f_NG = 0.5, beta = 1, k1 = 2.1 +- 0.1 Mpc^-1, (mu, t)
+# step 0.05; its models, not an estimate
+MODELS = {
+    "val384": {"ng": 384, "box": 215.0, "edges": [2.0, 2.2], "nmu": 10, "l_max": 6, "sigma_g": 0.1,
+               "f_ng": 0.5, "beta": 1.0, "index": -2.0},
 }
 N_SAMPLES = 4096
 
@@ -74,12 +85,31 @@ def golden_path(name):
     return os.path.join(HERE, f"{name}_oracle_B.npz")
 
 
+def write_models(name, threads):
+    """The discrete model [B]_d, the continuum [B]_c at each bin's mean
+    triangle and the discreteness weights w = [B]_d / [B]_c (even l)."""
+    m = MODELS[name]
+    A = synth.power_amplitude(m["ng"], m["box"], m["sigma_g"], m["index"])
+    edges = np.asarray(m["edges"], dtype=np.float64)
+    t0 = time.time()
+    r = O.discreteness_weights(m["ng"], m["box"], edges, m["nmu"], m["nmu"], m["l_max"], A, m["index"],
+                               m["f_ng"], m["beta"], nthreads=threads)
+    ev = lambda a: O.select_even(a, m["l_max"])
+    np.savez_compressed(golden_path(name), B_d=ev(r["d"]), B_c=ev(r["c"]), w=ev(r["w"]), k1_mu_t=r["k1_mu_t"],
+                        k1_edges=edges, ng=m["ng"], box_len=m["box"], n_mu=m["nmu"], n_t=m["nmu"],
+                        l_max=m["l_max"], A=A, index=m["index"], f_ng=m["f_ng"], beta=m["beta"],
+                        sigma_g=m["sigma_g"], oracle_wall_s=time.time() - t0)
+    print(f"{name}: wrote {golden_path(name)} ({time.time() - t0:.0f} s)", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("name", choices=sorted(CONFIGS))
+    ap.add_argument("name", choices=sorted(CONFIGS) + sorted(MODELS))
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--ckpt", default=None)
     args = ap.parse_args()
+    if args.name in MODELS:
+        return write_models(args.name, args.threads)
     cfg = CONFIGS[args.name]
     ckpt = args.ckpt or os.path.join(tempfile.gettempdir(), f"bisp_oracle_{args.name}.ckpt")
     t0 = time.time()

@@ -400,3 +400,25 @@ def test_discrete_model_matches_an_independent_evaluation():
     assert np.array_equal(fin, np.isfinite(got))
     scale = np.abs(want[fin]).max()
     assert np.abs(got[fin] - want[fin]).max() < 1e-10 * scale
+
+
+def test_discreteness_weights():
+    """w_l^m = [B]_d / [B]_c (Sec. III.C).  With an isotropic model and a
+    constant P every triangle has the same bispectrum, so the discrete and
+    continuum monopoles are both B^r and w_0^0 = 1 in every bin, whatever the
+    sampling; with beta != 0 the weights are the ratio of the two models at
+    each bin's mean triangle."""
+    ng, L = 32, 1000.0
+    edges = synth.default_k1_edges(ng, L, 3)
+    A, f_ng = 2.0, 0.5
+    r = O.discreteness_weights(ng, L, edges, 5, 5, 2, A, 0.0, f_ng, 0.0)
+    fin = np.isfinite(r["d"][..., 0])
+    assert fin.sum() > 10
+    assert np.abs(r["w"][..., 0][fin] - 1.0).max() < 1e-12
+    assert np.abs(r["d"][..., 0][fin] - 6 * f_ng * A * A).max() < 1e-12 * 6 * f_ng * A * A
+    r = O.discreteness_weights(ng, L, edges, 5, 5, 2, A, -2.0, f_ng, 1.0)
+    i = np.argwhere(fin)[0]
+    k1, mu, t = r["k1_mu_t"][tuple(i)]
+    c = O.continuum(A, -2.0, f_ng, 1.0, k1, mu, t, 2).real
+    assert np.allclose(r["c"][tuple(i)], c, rtol=1e-12)
+    assert np.allclose(r["w"][tuple(i)][0], r["d"][tuple(i)][0] / c[0], rtol=1e-12)
