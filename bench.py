@@ -345,6 +345,28 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+def systems_summary(args):
+    """The batched-mocks (c4) and served-trace (c5) workloads on this GPU,
+    summarised for the headline line (each is also its own workload)."""
+    import copy
+    import torch
+    a4 = copy.copy(args)
+    a4.workload, a4.steps, a4.warmup = "c4", 2, 3
+    l4 = run_batched(a4, emit=False)
+    torch.cuda.empty_cache()
+    a5 = copy.copy(args)
+    a5.workload = "c5"
+    l5 = run_serving(a5, emit=False)
+    torch.cuda.empty_cache()
+    keep4 = ("metric", "value", "unit", "ms_per_step", "single_job", "batched_over_single",
+             "results_identical_to_single_job", "device_status", "e2e")
+    keep5 = ("metric", "value", "unit", "ms_per_step", "served", "one_by_one", "served_over_one_by_one",
+             "launch_batch_sizes", "device_status")
+    return {"c4": dict({k: l4[k] for k in keep4}, workload=l4["config"]["workload"], mocks=l4["config"]["mocks"],
+                       batch_per_launch=l4["config"]["batch_per_launch"]),
+            "c5": dict({k: l5[k] for k in keep5}, workload=l5["config"]["workload"], server=l5["config"]["server"])}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -479,7 +501,9 @@ def run_ours(args):
                      "value_populated_bins": job_rate(populated, fields_per_step, ms / 1e3)},
             "vs_oracle": golden,
             "plan": {k: plan.info[k] for k in ("n_combos", "n_pairs", "n_items", "n_levels",
-                                                "triple_products", "dstore_bytes", "workspace_bytes")}}
+                                                "triple_products", "pair_products", "tc_row_points",
+                                                "tc_lane_points", "tc_mma_products", "dstore_bytes",
+                                                "workspace_bytes")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f64 = field.double().cpu().numpy()
         del ws
@@ -487,6 +511,11 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(W, edges, f64, plan.n_bins)
         if golden and golden.get("field_matches"):
             line["cpu_baseline"]["full_run"] = golden["oracle"] + " (the streamed oracle of the same definitions)"
+    if rank == 0 and world == 1 and args.workload == "c3" and not args.no_systems:
+        plan.close()
+        del out, field
+        torch.cuda.empty_cache()
+        line["systems"] = systems_summary(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -494,7 +523,7 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args):
+def run_batched(args, emit=True):
     """Batched mocks (c4): every mock of the workload through one plan, in
     batches of W["batch"] fields per launch, each batch a captured CUDA graph;
     beside it, the same mocks one by one through estimator_estimate (the
@@ -575,11 +604,13 @@ def run_batched(args):
             "batched_over_single": ms1 / ms, "results_identical_to_single_job": same,
             "device_status": status, "clocks": clk,
             "gpu_launches": len(graphs) * (3 + 2 * plan.info["n_levels"] + 3 + 2)}
-    if rank == 0:
+    if rank == 0 and emit:
         print(json.dumps(line), flush=True)
     for g in graphs:
         g.close()
-    return 0
+    plan.close()
+    plan1.close()
+    return line if not emit else 0
 
 
 def run_shells(args):
@@ -654,7 +685,7 @@ def run_shells(args):
     return 0
 
 
-def run_serving(args):
+def run_serving(args, emit=True):
     """Serving (c5): the seeded 300-request Poisson trace through the serving
     loop (resident plans, continuous batching on 4 streams, HBM budget), then
     the same trace one request at a time on one stream (the plain
@@ -695,9 +726,10 @@ def run_serving(args):
             "data": "synthetic", "config": cfg, "served": served, "one_by_one": single,
             "served_over_one_by_one": served["configs_per_s"] / single["configs_per_s"],
             "launch_batch_sizes": dict(sorted(batches.items())), "device_status": status, "clocks": clk}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     srv.close()
-    return 0
+    return line if not emit else 0
 
 
 def launch_decision(gpus: int, env) -> tuple:
@@ -820,6 +852,8 @@ def main(argv=None):
                          "m0: the spherical-shell m = 0 estimator against the ring/plane one at 64^3; "
                          "val: the paper's validation, 50 realisations at 384^3 against [B]_d")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="c3 at N = 1: skip the batched (c4) and served (c5) summaries added to the line")
     ap.add_argument("--split", default="shares", choices=["replicas", "shares"],
                     help="N > 1: shares (one field's Step II split over the ranks, one all-reduce of the "
                          "output; strong scaling; the default) or replicas (a field per rank, weak scaling)")

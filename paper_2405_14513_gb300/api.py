@@ -41,7 +41,9 @@ class PlanInfo(C.Structure):
                 ("n_levels", C.c_int), ("n_bins", C.c_int64), ("n_combos", C.c_int64),
                 ("n_pairs", C.c_int64), ("n_items", C.c_int64), ("triple_products", C.c_double),
                 ("dstore_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t),
-                ("resident_bytes", C.c_size_t), ("n_views", C.c_int), ("out_doubles", C.c_int64)]
+                ("resident_bytes", C.c_size_t), ("n_views", C.c_int), ("out_doubles", C.c_int64),
+                ("pair_products", C.c_double), ("tc_row_points", C.c_double), ("tc_lane_points", C.c_double),
+                ("tc_mma_products", C.c_double)]
 
 
 class ViewInfo(C.Structure):

@@ -771,6 +771,16 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->resident_bytes = p->resident;
     info->n_views = int(P.views.size());
     info->out_doubles = P.n_out;
+    info->pair_products = P.pair_products;
+    info->tc_row_points = 0;
+    info->tc_lane_points = 0;
+    info->tc_mma_products = P.tensor ? P.tc_mma_products : 0;
+    if (P.tensor)
+        for (const TcTile &T : P.tc_tiles) {
+            const double m2 = double(T.M) * T.M;
+            info->tc_row_points += double(T.nrow) * m2;
+            info->tc_lane_points += double(kTcRows) * m2;
+        }
     return BISP_OK;
 }
 

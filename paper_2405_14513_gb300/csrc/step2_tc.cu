@@ -234,6 +234,92 @@ __device__ __forceinline__ void form_a(const unsigned char *u8, const unsigned c
     }
 }
 
+// What a compute warp's stage loop needs (see k_step2_tc).
+struct CompArgs {
+    unsigned char *sS, *sHi, *sLo;
+    uint32_t tlane;            // tensor-memory address of lane 0 of this warp's quarter
+    volatile int *abort;
+    TcSync *sy;
+    int rowb, nslot, S, nstage, spins, t, half, s1, s2;
+};
+
+// The stage loop of one compute thread: form A (its row's 8 points of the
+// stage) and its share of B, then add the accumulators of the stage before.
+// Returns false if a wait gave up.  B piece p (grid points 2p, 2p + 1) of
+// column c goes to core matrix (K block p, rows 8 (c / 8) ..), row c % 8;
+// this thread's pieces are i = t and t + 256 (i = p NC + c), fixed for the
+// tile, so their offsets are computed once.
+template <int NC, bool G1, bool G2, bool G3>
+__device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC / 2])
+{
+    constexpr int NH = NC / 2;
+    constexpr int NB = NC / 8;
+    constexpr int BB = NC * kTX * 8;
+    constexpr int NP = (NC * 8 + kCompute - 1) / kCompute;    // B pieces per thread (at most 2)
+    TcSync *sy = ca.sy;
+    int src[NP], dst[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        const int i = ca.t + k * kCompute;
+        const int c = i % NC, p = i / NC;
+        src[k] = i < NC * 8 ? (ca.nslot + c) * kSlotBytes + p * 16 : -1;
+        dst[k] = (p * NB + c / 8) * 128 + (c % 8) * 16;
+    }
+    const int uoff = ca.s1 * kSlotBytes, voff = ca.s2 * kSlotBytes;
+#pragma unroll
+    for (int c = 0; c < NH; ++c) acc[c] = 0.f;
+    bool ok = true;
+    int q = 0;                                   // ring buffer of stage st
+    uint32_t ph = 0;                             // its phase: (st / S) & 1
+    const unsigned char *sq = ca.sS;             // ring buffer q
+    for (int st = 0; st <= ca.nstage; ++st) {
+        if (st < ca.nstage) {
+            const int b = st & 1;
+            ok = mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins);
+            if (!ok) break;
+            form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * b, ca.half);
+            // B, high and low parts, in the canonical layout.  Buffer b was
+            // last read by the MMAs of stage st - 2, complete: their
+            // accumulators were read at stage st - 1.
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                if (src[k] < 0) continue;
+                const float4 v = *reinterpret_cast<const float4 *>(sq + src[k]);
+                const int o = b * BB + dst[k];
+                *reinterpret_cast<float4 *>(ca.sHi + o) = v;
+                uint4 l;
+                lo2(v.x, v.y, l.x, l.y);
+                lo2(v.z, v.w, l.z, l.w);
+                *reinterpret_cast<uint4 *>(ca.sLo + o) = l;
+            }
+            mbar_arrive(&sy->empty[q]);
+            if (++q == ca.S) {
+                q = 0;
+                ph ^= 1u;
+                sq = ca.sS;
+            } else {
+                sq += ca.rowb;
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&sy->aready[b]);
+        }
+        if (st > 0) {
+            // accumulators of stage st - 1 (buffer b)
+            const int b = (st - 1) & 1;
+            const uint32_t par = uint32_t((st - 1) >> 1) & 1;
+            ok = mbar_wait_abort(&sy->mdone[b], par, ca.abort, ca.spins);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            add_accumulator<NH>(ca.tlane + 128 + 64 * b + NH * ca.half, acc);
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            mbar_arrive(&sy->dfree[b]);
+        }
+    }
+    return ok;
+}
+
 // Two blocks per SM (sharing its 227 KB of shared memory and 512
 // tensor-memory columns) hold 22 warps, 6 on some of the SM's four
 // schedulers, whose register files are 16384 each: at most 80 registers a
@@ -377,71 +463,26 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         __syncwarp();
     } else {
         // compute warps: the thread owns tensor-memory lane (row) 32 (warp % 4)
-        // + lane; rows past the tile's end read the zero row
-        constexpr int NH = NC / 2;               // accumulator columns of this thread
+        // + lane; rows past the tile's end read the zero row.  The loop is
+        // instantiated per sign pattern (uniform over the tile; n1 >= 0)
         const int quarter = warp & 3, half = warp >> 2;
         const int row = quarter * 32 + lane;
         const bool live = row < T.nrow;
         TcRow R{};
         if (live) R = args.rows[T.row0 + row];
-        const int s1 = live ? R.s1 : nf, s2 = live ? R.s2 : nf;
-        const uint32_t tlane = tmem + (uint32_t(quarter * 32) << 16);
-        float acc[NH];
-#pragma unroll
-        for (int c = 0; c < NH; ++c) acc[c] = 0.f;
-        int q = 0;                               // ring buffer of stage st
-        uint32_t ph = 0;                         // its phase: (st / S) & 1
-        for (int st = 0; st <= nstage && ok; ++st) {
-            if (st < nstage) {
-                const int b = st & 1;
-                ok = mbar_wait_abort(&sy->full[q], ph, abort, spins);
-                if (!ok) break;
-                const unsigned char *sq = sS + q * rowb;
-                const unsigned char *u8 = sq + s1 * kSlotBytes, *v8 = sq + s2 * kSlotBytes;
-                const uint32_t a = tlane + 64 * b;
-                switch (T.flags) {   // uniform over the tile; n1 >= 0 (half space)
-                case 0: form_a<false, false, false>(u8, v8, a, half); break;
-                case 2: form_a<false, true, false>(u8, v8, a, half); break;
-                case 4: form_a<false, false, true>(u8, v8, a, half); break;
-                default: form_a<false, true, true>(u8, v8, a, half); break;
-                }
-                // B, high and low parts, in the canonical layout: piece p (grid
-                // points 2p, 2p + 1) of column c goes to core matrix (K block p,
-                // rows 8 (c / 8) ..), row c % 8.  Buffer b was last read by the
-                // MMAs of stage st - 2, complete: their accumulators were read
-                // at stage st - 1.
-                for (int i = t; i < NC * 8; i += kCompute) {
-                    const int c = i % NC, p = i / NC;
-                    const float4 v = *reinterpret_cast<const float4 *>(sq + (nslot + c) * kSlotBytes + p * 16);
-                    const int o = b * BB + (p * NB + c / 8) * 128 + (c % 8) * 16;
-                    *reinterpret_cast<float4 *>(sHi + o) = v;
-                    uint4 l;
-                    lo2(v.x, v.y, l.x, l.y);
-                    lo2(v.z, v.w, l.z, l.w);
-                    *reinterpret_cast<uint4 *>(sLo + o) = l;
-                }
-                mbar_arrive(&sy->empty[q]);
-                if (++q == S) { q = 0; ph ^= 1u; }
-                asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(&sy->aready[b]);
-            }
-            if (st > 0) {
-                // accumulators of stage st - 1 (buffer b)
-                const int b = (st - 1) & 1;
-                const uint32_t par = uint32_t((st - 1) >> 1) & 1;
-                ok = mbar_wait_abort(&sy->mdone[b], par, abort, spins);
-                if (!ok) break;
-                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                add_accumulator<NH>(tlane + 128 + 64 * b + NH * half, acc);
-                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-                mbar_arrive(&sy->dfree[b]);
-            }
+        CompArgs ca{sS, sHi, sLo, tmem + (uint32_t(quarter * 32) << 16), abort, sy, rowb, nslot, S, nstage, spins,
+                    t, half, live ? int(R.s1) : nf, live ? int(R.s2) : nf};
+        float acc[NC / 2];
+        switch (T.flags) {
+        case 0: ok = compute_loop<NC, false, false, false>(ca, acc); break;
+        case 2: ok = compute_loop<NC, false, true, false>(ca, acc); break;
+        case 4: ok = compute_loop<NC, false, false, true>(ca, acc); break;
+        default: ok = compute_loop<NC, false, true, true>(ca, acc); break;
         }
         if (live) {
             double *dst = args.partials + R.p0 + int64_t(U.chunk) * R.stride;
             const double nan = __longlong_as_double(0x7FF8000000000000LL);
+            constexpr int NH = NC / 2;
 #pragma unroll
             for (int c = 0; c < NH; ++c) {
                 const int j = c + NH * half - int(R.col0);
