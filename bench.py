@@ -172,16 +172,21 @@ STEP2_SOURCE = {
 
 def _traffic(ng, precision):
     """DRAM bytes of Step II per estimate from the committed ncu summary, if
-    it was taken on the kernel source as it is now."""
+    it was taken at this grid size on the kernel source as it is now.
+    Returns (bytes, how) or (None, why)."""
     p = os.path.join(ROOT, "profiles", f"step2_dram_{precision}.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
-        if d.get("kernel_digest") != _kernel_digest(precision) or int(d.get("n_g", ng)) != ng:
-            return None
-        return float(d["bytes_per_estimate"])
+        if d.get("kernel_digest") != _kernel_digest(precision):
+            return None, "the kernel changed since the DRAM capture"
+        if int(d["n_g"]) == ng:
+            return float(d["bytes_per_estimate"]), f"ncu capture at {ng}^3 ({d.get('source', '')})"
+        # a smaller grid is not scaled: its L2 hit rate differs (the D store
+        # of 256^3 is 1.8 GB, that of 512^3 17.9 GB)
+        return None, f"no capture at {ng}^3"
     except (OSError, ValueError, KeyError):
-        return None
+        return None, "no capture"
 
 
 def _kernel_digest(precision):
@@ -472,8 +477,9 @@ def run_ours(args):
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"kernel": "k_step2 (Step II triple sums, FP32 FMA)", "bound": "alu",
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"}
+    traffic, traffic_how = _traffic(ng, args.precision)
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": _traffic(ng, args.precision), "flops_per_estimate": flops["step2"],
+                 "traffic": traffic, "traffic_source": traffic_how, "flops_per_estimate": flops["step2"],
                  "ms_per_estimate": s2_ms, "launches_per_estimate": st_n["step2"] / args.steps})
     # Step I (HBM-bound transforms): algorithmic bytes = the D store written
     # once + the kept planes of Delta read once, over its own event time
@@ -502,7 +508,8 @@ def run_ours(args):
             "vs_oracle": golden,
             "plan": {k: plan.info[k] for k in ("n_combos", "n_pairs", "n_items", "n_levels",
                                                 "triple_products", "pair_products", "tc_row_points",
-                                                "tc_lane_points", "tc_mma_products", "dstore_bytes",
+                                                "tc_lane_points", "tc_mma_products", "tc_staged_bytes",
+                                                "dstore_bytes",
                                                 "workspace_bytes")}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         f64 = field.double().cpu().numpy()

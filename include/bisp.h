@@ -104,6 +104,7 @@ typedef struct {
     double tc_row_points;            /* pair products the tiles form (rows x points)   */
     double tc_lane_points;           /* tensor-memory lanes x points of all tiles      */
     double tc_mma_products;          /* lanes x window columns x points (MMA work)     */
+    double tc_staged_bytes;          /* bytes the tiles copy from L2 into shared memory */
 } bisp_plan_info;
 
 /* A binning of the output.  Consecutive even l with the same (mu, t) grid

@@ -43,7 +43,7 @@ class PlanInfo(C.Structure):
                 ("dstore_bytes", C.c_size_t), ("workspace_bytes", C.c_size_t),
                 ("resident_bytes", C.c_size_t), ("n_views", C.c_int), ("out_doubles", C.c_int64),
                 ("pair_products", C.c_double), ("tc_row_points", C.c_double), ("tc_lane_points", C.c_double),
-                ("tc_mma_products", C.c_double)]
+                ("tc_mma_products", C.c_double), ("tc_staged_bytes", C.c_double)]
 
 
 class ViewInfo(C.Structure):

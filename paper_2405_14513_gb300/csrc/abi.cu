@@ -775,11 +775,14 @@ int estimator_plan_info(const bisp_plan *p, bisp_plan_info *info)
     info->tc_row_points = 0;
     info->tc_lane_points = 0;
     info->tc_mma_products = P.tensor ? P.tc_mma_products : 0;
+    info->tc_staged_bytes = 0;
     if (P.tensor)
         for (const TcTile &T : P.tc_tiles) {
             const double m2 = double(T.M) * T.M;
             info->tc_row_points += double(T.nrow) * m2;
             info->tc_lane_points += double(kTcRows) * m2;
+            // every stage stages each slot and window field (16 points, 8 bytes each)
+            info->tc_staged_bytes += double(T.nslot + T.ncol) * m2 * 8.0;
         }
     return BISP_OK;
 }
