@@ -167,6 +167,24 @@ int estimator_estimate(bisp_plan *plan, const void *delta, int batch, void *work
 int estimator_estimate_host(bisp_plan *plan, const void *delta_host, int batch, double *B_host,
                             void *stream);
 
+/* Streaming estimates from and to HOST memory, for a caller with a sequence
+ * of fields in host memory: the copy of each field in overlaps the estimate
+ * of the one before.  estimator_host_submit queues the copy of delta_host to
+ * the device (on a copy stream the plan owns), the estimate and the copy of
+ * its B to B_host (on `stream`) and returns at once; estimator_host_wait
+ * returns when the oldest submission's B_host is complete, with its wait
+ * status (as estimator_workspace_status).  At most two submissions are in
+ * flight (a third submit is BISP_INVALID_ARG; a wait with none is
+ * BISP_INVALID_ARG).  delta_host ([batch][N_g]^3 as for estimator_estimate)
+ * and B_host ([batch][out_doubles]) must stay valid and unchanged until the
+ * submission's wait returns; page-locked host memory makes the copies
+ * asynchronous.  Submit on one stream; the plan allocates (once) two input
+ * and two output buffers and shares its workspace with
+ * estimator_estimate_host, so the two host forms must not overlap.  (The
+ * paper has no counterpart: it reads each field from disk.) */
+int estimator_host_submit(bisp_plan *plan, const void *delta_host, int batch, double *B_host, void *stream);
+int estimator_host_wait(bisp_plan *plan, void *stream);
+
 /* One share of an estimate, for splitting one field over several devices
  * (each holding its own plan).  The numerator of Eq. bs_lm2_1 is a sum over
  * combinations of Re Y_lm S (S of Eq. fftbs), so it splits over any

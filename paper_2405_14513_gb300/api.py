@@ -71,6 +71,10 @@ def load():
         lib.estimator_estimate.restype = C.c_int
         lib.estimator_estimate_host.argtypes = [vp, vp, C.c_int, vp, vp]
         lib.estimator_estimate_host.restype = C.c_int
+        lib.estimator_host_submit.argtypes = [vp, vp, C.c_int, vp, vp]
+        lib.estimator_host_submit.restype = C.c_int
+        lib.estimator_host_wait.argtypes = [vp, vp]
+        lib.estimator_host_wait.restype = C.c_int
         lib.estimator_estimate_part.argtypes = [vp, vp, C.c_int, vp, vp, C.c_int, C.c_int, vp]
         lib.estimator_estimate_part.restype = C.c_int
         lib.estimator_stats_update.argtypes = [vp, C.c_int, C.c_int64, vp, vp, vp, vp]
@@ -183,6 +187,7 @@ class Plan:
         self.n_k1 = len(self._edges) - 1
         self.precision = precision
         self.max_batch = max_batch
+        self._inflight = []              # host arrays of estimator_host_submit calls not yet waited for
         d = Desc(n_g, box_len, self.n_k1, _dp(self._edges), n_mu, n_t, l_max,
                  PRECISIONS[precision], max_batch)
         if mu_t_bins_l is not None:
@@ -296,6 +301,31 @@ class Plan:
                                            _stream_handle(stream))
         _check(st, "estimator_graph_create")
         return Graph(h, (delta, workspace, out))
+
+    def host_submit(self, delta: np.ndarray, out: np.ndarray, stream=None):
+        """Queue the estimate of a host field (see estimator_host_submit):
+        delta [batch][N][N][N] (float32, or float64 for fp64; page-locked for
+        overlap), out float64 [batch][out_doubles]; both stay referenced until
+        the matching host_wait."""
+        d = np.asarray(delta)
+        if d.ndim == 3:
+            d = d[None]
+        dt = np.float64 if self.precision == "fp64" else np.float32
+        if d.dtype != dt or not d.flags.c_contiguous or d.shape[1:] != (self.n_g,) * 3:
+            raise ValueError(f"delta must be a contiguous {np.dtype(dt).name} [batch][N][N][N] array")
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < d.shape[0] * self.info["out_doubles"]:
+            raise ValueError("out must be a contiguous float64 array of batch x out_doubles")
+        _check(load().estimator_host_submit(self._h, C.c_void_p(d.ctypes.data), d.shape[0],
+                                            C.c_void_p(out.ctypes.data), _stream_handle(stream)),
+               "estimator_host_submit")
+        self._inflight.append((d, out))
+
+    def host_wait(self, stream=None):
+        """Wait for the oldest host submission; returns its output array."""
+        st = load().estimator_host_wait(self._h, _stream_handle(stream))
+        d, out = self._inflight.pop(0) if self._inflight else (None, None)
+        _check(st, "estimator_host_wait")
+        return out
 
     def estimate_host(self, delta: np.ndarray, out: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Host-memory variant: numpy in, numpy out (copies inside the call)."""

@@ -97,6 +97,18 @@ struct bisp_plan {
     // buffers of estimator_estimate_host
     void *own_ws = nullptr, *own_in = nullptr;
     double *own_out = nullptr;
+    // streaming from host memory (estimator_host_submit / _wait): two slots,
+    // each with its input and output buffers; the input copies run on a
+    // stream of the plan's own, the estimates on the caller's stream
+    struct HostPipe {
+        cudaStream_t copy = nullptr;
+        void *in[2] = {};
+        double *out[2] = {};
+        int *status_h = nullptr;                  // pinned: [2][max_batch] wait-status words
+        cudaEvent_t in_ready[2] = {}, in_free[2] = {}, done[2] = {};
+        int batch[2] = {};
+        int head = 0, count = 0;                  // oldest slot in flight; submissions in flight
+    } pipe;
     // stage timing
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -196,6 +208,16 @@ void free_plan(bisp_plan *p)
     if (p->own_ws) cudaFree(p->own_ws);
     if (p->own_in) cudaFree(p->own_in);
     if (p->own_out) cudaFree(p->own_out);
+    auto &h = p->pipe;
+    for (int i = 0; i < 2; ++i) {
+        if (h.in[i]) cudaFree(h.in[i]);
+        if (h.out[i]) cudaFree(h.out[i]);
+        if (h.in_ready[i]) cudaEventDestroy(h.in_ready[i]);
+        if (h.in_free[i]) cudaEventDestroy(h.in_free[i]);
+        if (h.done[i]) cudaEventDestroy(h.done[i]);
+    }
+    if (h.status_h) cudaFreeHost(h.status_h);
+    if (h.copy) cudaStreamDestroy(h.copy);
     delete p;
 }
 
@@ -287,7 +309,8 @@ int compute_ntri(bisp_plan *p, cudaStream_t s)
             CK(cudaMemcpyAsync(d_joff, joff.data(), joff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
             CK(launch_ring_gather<double>(I, R.ng, p->ring_arg, d_jobs, int64_t(jobs[lv].size()), M, true, gt,
                                           p->tw_d, Batch{}, s));
-            CK(launch_fft_cols<double>(gt, I, M, int64_t(jobs[lv].size()), d_joff, p->tw_d, Batch{}, s));
+            CK(launch_fft_cols<double>(gt, I, M, int64_t(jobs[lv].size()), d_joff, d_jobs, p->ring_arg, p->tw_d, Batch{},
+                                        s));
             CK(cudaStreamSynchronize(s));   // the job tables are reused by the next grid
         }
         CK(launch_ntri(I, d_ioff, d_tri, int64_t(tri.size() / 4), p->grid_arg, d_raw, s));
@@ -441,7 +464,7 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
             return launch_ring_gather<R>(planes, ng, p->ring_arg, p->d_jobs[l], nj, L.M, false, b0, tw, one, s, rt);
         });
         const int r = pick_w(L.M, [&](int w) {
-            return launch_fft_cols<R>(b0, b1, L.M, nj, d_off, tw, one, s, w);
+            return launch_fft_cols<R>(b0, b1, L.M, nj, d_off, p->d_jobs[l], p->ring_arg, tw, one, s, w);
         });
         if (g < 0 || r < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
         p->rt_gather[L.lev] = std::max(g, 0);
@@ -658,7 +681,8 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
             const int M = L.M;
             CK(launch_ring_gather<R>(A_, ng, p->ring_arg, p->d_jobs[l], L.njobs, M, false, gt, tw, region, s,
                                      p->rt_gather[L.lev]));
-            CK(launch_fft_cols<R>(gt, dstore, M, L.njobs, p->d_job_off[l], tw, region, s, p->rt_rows[L.lev]));
+            CK(launch_fft_cols<R>(gt, dstore, M, L.njobs, p->d_job_off[l], p->d_jobs[l], p->ring_arg, tw, region, s,
+                                  p->rt_rows[L.lev]));
         }
     }
     {   // Step II: triple sums (Eq. fftbs), all units or one share of them
@@ -859,6 +883,70 @@ int estimator_estimate_host(bisp_plan *p, const void *delta_host, int batch, dou
     if (st) return st;
     CK(cudaMemcpyAsync(B_host, p->own_out, outb * batch, cudaMemcpyDeviceToHost, s));
     return estimator_workspace_status(p, p->own_ws, batch, stream);
+}
+
+int estimator_host_submit(bisp_plan *p, const void *delta_host, int batch, double *B_host, void *stream)
+{
+    g_err.clear();
+    if (!p || !delta_host || !B_host) return fail(BISP_INVALID_ARG, "NULL argument");
+    if (batch < 1 || batch > p->hp.desc.max_batch) return fail(BISP_INVALID_ARG, "batch out of range");
+    auto &h = p->pipe;
+    if (h.count == 2) return fail(BISP_INVALID_ARG, "two submissions in flight: call estimator_host_wait first");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const HostPlan &P = p->hp;
+    const int mb = P.desc.max_batch;
+    const size_t field = size_t(P.desc.n_g) * P.desc.n_g * P.desc.n_g *
+                         (p->precision == BISP_PREC_FP64 ? sizeof(double) : sizeof(float));
+    const size_t outb = size_t(P.n_out) * sizeof(double);
+    if (!h.copy) {
+        if (!p->own_ws) CK(cudaMalloc(&p->own_ws, std::max<size_t>(size_t(mb) * p->region_bytes, 256)));
+        CK(cudaStreamCreateWithFlags(&h.copy, cudaStreamNonBlocking));
+        CK(cudaMallocHost((void **)&h.status_h, sizeof(int) * 2 * size_t(mb)));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaMalloc(&h.in[i], field * mb));
+            CK(cudaMalloc((void **)&h.out[i], outb * mb));
+            CK(cudaEventCreateWithFlags(&h.in_ready[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h.in_free[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h.done[i], cudaEventDisableTiming));
+        }
+    }
+    const int k = (h.head + h.count) % 2;       // the slot of this submission
+    // input copy on the plan's copy stream, once the estimate that last read
+    // this slot's input is done (an event not yet recorded is no wait)
+    CK(cudaStreamWaitEvent(h.copy, h.in_free[k], 0));
+    CK(cudaMemcpyAsync(h.in[k], delta_host, field * batch, cudaMemcpyHostToDevice, h.copy));
+    CK(cudaEventRecord(h.in_ready[k], h.copy));
+    // the estimate, its wait status and the output copy on the caller's stream
+    CK(cudaStreamWaitEvent(s, h.in_ready[k], 0));
+    int st = dispatch_estimate(p, h.in[k], batch, p->own_ws, h.out[k], s);
+    if (st) return st;
+    CK(cudaEventRecord(h.in_free[k], s));
+    CK(cudaMemcpy2DAsync(h.status_h + size_t(k) * mb, sizeof(int),
+                         static_cast<unsigned char *>(p->own_ws) + p->off_status, p->region_bytes, sizeof(int),
+                         size_t(batch), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(B_host, h.out[k], outb * batch, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(h.done[k], s));
+    h.batch[k] = batch;
+    ++h.count;
+    return BISP_OK;
+}
+
+int estimator_host_wait(bisp_plan *p, void *stream)
+{
+    (void)stream;
+    g_err.clear();
+    if (!p) return fail(BISP_INVALID_ARG, "NULL plan");
+    auto &h = p->pipe;
+    if (h.count == 0) return fail(BISP_INVALID_ARG, "no submission in flight");
+    const int k = h.head;
+    CK(cudaEventSynchronize(h.done[k]));
+    h.head = (h.head + 1) % 2;
+    --h.count;
+    int bad = 0;
+    const int mb = p->hp.desc.max_batch;
+    for (int f = 0; f < h.batch[k]; ++f) bad |= h.status_h[size_t(k) * mb + f] != 0;
+    if (bad) return fail(BISP_TIMEOUT, "a tensor-core Step-II block gave up a bounded wait; its sums are NaN");
+    return BISP_OK;
 }
 
 }  // extern "C"

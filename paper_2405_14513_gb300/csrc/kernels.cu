@@ -309,6 +309,10 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     const int mc = rings.maxc[J.r];
     const int row0 = tile * rt;
     const int nr = min(rt, M - row0);
+    // rows i hold ring members only where |u_x| <= maxc for u_x = i or i - M;
+    // a block of rows without members is zero after the transform too, and
+    // the column pass reads such rows as zero without loading them
+    if (row0 > mc && row0 + nr - 1 < M - mc) return;
     DivIter ld(threadIdx.x, blockDim.x, M);
     for (int t = threadIdx.x; t < nr * M; t += blockDim.x, ld.next()) {
         const int tr = ld.q, j = ld.r;
@@ -355,7 +359,8 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restrict__ out, int M, int ntile, int w,
-           const int64_t *__restrict__ out_off, Twiddles<typename Cx<R>::T> tw, int64_t fs)
+           const int64_t *__restrict__ out_off, const Job *__restrict__ jobs, RingArg rings,
+           Twiddles<typename Cx<R>::T> tw, int64_t fs)
 {
     using C = typename Cx<R>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -368,10 +373,11 @@ k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restri
     const int c0 = int(blockIdx.x - jb * ntile) * w;
     const int nc = min(w, M - c0);
     const C *src = in + jb * int64_t(M) * M + c0;
+    const int mc = rings.maxc[jobs[jb].r];      // rows mc < i < M - mc hold no ring member: zero
     DivIter ld(threadIdx.x, blockDim.x, nc);
     for (int t = threadIdx.x; t < M * nc; t += blockDim.x, ld.next()) {
         const int i = ld.q, c = ld.r;
-        a[c * P + i] = src[int64_t(i) * M + c];
+        a[c * P + i] = (i <= mc || i >= M - mc) ? src[int64_t(i) * M + c] : cmk<C>(0.0, 0.0);
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nc, tw);
@@ -750,8 +756,8 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
 
 template <typename R>
 cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int64_t njobs,
-                            const int64_t *out_off, const Twiddles<typename Cx<R>::T> &tw, const Batch &fb,
-                            cudaStream_t s, int w)
+                            const int64_t *out_off, const Job *jobs, const RingArg &rings,
+                            const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int w)
 {
     using C = typename Cx<R>::T;
     if (w <= 0) w = 8;
@@ -761,7 +767,8 @@ cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out,
     const int ntile = (M + w - 1) / w;
     const int64_t nblk = njobs * ntile;
     if (nblk == 0) return cudaSuccess;
-    k_fft_cols<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, M, ntile, w, out_off, tw, fb.fs_in);
+    k_fft_cols<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, M, ntile, w, out_off, jobs, rings, tw,
+                                                                 fb.fs_in);
     return cudaGetLastError();
 }
 
@@ -900,9 +907,11 @@ template cudaError_t launch_fft_rows_T<float>(const float2 *, float2 *, int, int
 template cudaError_t launch_fft_rows_T<double>(const double2 *, double2 *, int, int, int64_t, const int64_t *, double, bool, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<float>(const float2 *, int, const RingArg &, const Job *, int64_t, int, bool, float2 *, const Twiddles<float2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_ring_gather<double>(const double2 *, int, const RingArg &, const Job *, int64_t, int, bool, double2 *, const Twiddles<double2> &, const Batch &, cudaStream_t, int);
-template cudaError_t launch_fft_cols<float>(const float2 *, float2 *, int, int64_t, const int64_t *, const Twiddles<float2> &,
+template cudaError_t launch_fft_cols<float>(const float2 *, float2 *, int, int64_t, const int64_t *, const Job *,
+                                            const RingArg &, const Twiddles<float2> &,
                                             const Batch &, cudaStream_t, int);
-template cudaError_t launch_fft_cols<double>(const double2 *, double2 *, int, int64_t, const int64_t *,
+template cudaError_t launch_fft_cols<double>(const double2 *, double2 *, int, int64_t, const int64_t *, const Job *,
+                                             const RingArg &,
                                              const Twiddles<double2> &, const Batch &, cudaStream_t, int);
 template cudaError_t launch_step2<float>(const StepIIArgs &, const float2 *, const int64_t *, const int64_t *, int,
                                          cudaStream_t);

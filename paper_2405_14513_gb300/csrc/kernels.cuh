@@ -90,11 +90,13 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
 
 // Step I second pass: for each of njobs M x M fields in gt ([u_x][k_y],
 // the gather's output), transforms along u_x in strips of w columns and
-// writes the field [k_x][k_y] at out + out_off[job].
+// writes the field [k_x][k_y] at out + out_off[job].  Rows that hold no
+// member of the job's ring (jobs[job].r, its largest |u_x| in rings) are
+// taken as zero without being read (the gather does not write them).
 template <typename R>
 cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out, int M, int64_t njobs,
-                            const int64_t *out_off, const Twiddles<typename Cx<R>::T> &tw, const Batch &fb,
-                            cudaStream_t s, int w = 0);
+                            const int64_t *out_off, const Job *jobs, const RingArg &rings,
+                            const Twiddles<typename Cx<R>::T> &tw, const Batch &fb, cudaStream_t s, int w = 0);
 
 // Step II: partial triple sums of units, one block per unit, one launch per
 // block class (units [lo[c], hi[c]) run in blocks of 2^c warps with

@@ -511,3 +511,31 @@ def test_tensor_core_waits_give_up_and_the_plan_recovers():
     assert plan.workspace_status(ws, 1) == 0
     assert np.array_equal(again, ref, equal_nan=True) and np.array_equal(good, ref, equal_nan=True)
     plan.close()
+
+
+def test_host_streaming_equals_host_estimates():
+    """estimator_host_submit / estimator_host_wait: fields from host memory,
+    the copy of one overlapping the estimate of the other, give the bits of
+    estimator_estimate_host for each field; a third submission in flight and
+    a wait with none are refused."""
+    ng, L = 32, 600.0
+    plan = api.Plan(ng, L, synth.default_k1_edges(ng, L, 3), 5, 5, 6, precision="mixed_tc", max_batch=2)
+    fields = [torch.from_numpy(synth.make_field(ng, L, s).astype(np.float32)).pin_memory().numpy()
+              for s in (5, 6, 7)]
+    want = [plan.estimate_host(f) for f in fields]
+    outs = [torch.empty(int(np.prod(plan.out_shape(1))), dtype=torch.float64).pin_memory().numpy()
+            for _ in fields]
+    stream = torch.cuda.current_stream()
+    plan.host_submit(fields[0], outs[0], stream)
+    plan.host_submit(fields[1], outs[1], stream)
+    with pytest.raises(api.BispError):
+        plan.host_submit(fields[2], outs[2], stream)
+    got0 = plan.host_wait(stream)
+    plan.host_submit(fields[2], outs[2], stream)
+    got1 = plan.host_wait(stream)
+    got2 = plan.host_wait(stream)
+    with pytest.raises(api.BispError):
+        plan.host_wait(stream)
+    for g, w in zip((got0, got1, got2), want):
+        assert np.array_equal(g.reshape(w.shape), w, equal_nan=True)
+    plan.close()
