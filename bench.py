@@ -625,7 +625,7 @@ def run_batched(args, emit=True):
                            "ms_per_step": ms1, "form": "estimator_estimate, one mock per call, no graph"},
             "batched_over_single": ms1 / ms, "results_identical_to_single_job": same,
             "device_status": status, "clocks": clk,
-            "gpu_launches": len(graphs) * (3 + 2 * plan.info["n_levels"] + 3 + 2)}
+            "gpu_launches": len(graphs) * (3 + 2 * plan.info["n_levels"] + 3 + 3)}
     if rank == 0 and emit:
         print(json.dumps(line), flush=True)
     for g in graphs:

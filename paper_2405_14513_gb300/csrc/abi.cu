@@ -74,6 +74,7 @@ struct bisp_plan {
     int64_t *d_doff = nullptr;
     Record *d_rec = nullptr;
     int64_t *d_bin_start = nullptr;
+    int64_t *d_chunk_lo = nullptr, *d_chunk_hi = nullptr, *d_bin_chunk = nullptr;   // binning chunks
     double *d_den = nullptr;
     std::vector<double> h_den;
     Twiddles<float2> tw_f{};             // transform twiddles (device tables)
@@ -86,7 +87,9 @@ struct bisp_plan {
     // uses bytes [f region_bytes, (f + 1) region_bytes) of the workspace
     // off_status: one int, set by a Step-II block of this field whose bounded
     // wait ran out; cleared at the start of every estimate
-    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, off_status = 0, region_bytes = 0;
+    // off_epi: the binning's partial sums per chunk
+    size_t off_a = 0, off_b = 0, off_gt = 0, off_dstore = 0, off_part = 0, off_S = 0, off_status = 0, off_epi = 0,
+           region_bytes = 0;
     int wait_spins = kDefaultWaitSpins;  // bound of the tensor-core Step II's abortable waits
     int device = -1;                     // the device the plan's tables live on
     int last_field = 0;                  // field of the last estimate that introspection reads
@@ -571,28 +574,39 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     if (!st) st = upload(p, &p->d_doff, P.doff, s);
     if (!st) st = upload(p, &p->d_rec, P.records, s);
     if (!st) st = upload(p, &p->d_bin_start, P.bin_start, s);
+    if (!st) st = upload(p, &p->d_chunk_lo, P.chunk_lo, s);
+    if (!st) st = upload(p, &p->d_chunk_hi, P.chunk_hi, s);
+    if (!st) st = upload(p, &p->d_bin_chunk, P.bin_chunk, s);
     if (!st) st = dev_alloc(p, &p->d_den, size_t(P.n_out));
     if (st) return st;
+    const int64_t epi_nlm = int64_t(desc->l_max / 2 + 1) * (desc->l_max / 2 + 1);   // moments of l <= l_max
     // plan-time denominators of Eq. bs_lm2_1 (FP64)
     {
-        double *d_nt = nullptr;
-        void *q = nullptr;
-        if (cudaMalloc(&q, std::max<size_t>(P.rec_ntri.size() * sizeof(double), 16)) != cudaSuccess) {
+        double *d_nt = nullptr, *d_epi = nullptr;
+        void *q = nullptr, *q2 = nullptr;
+        if (cudaMalloc(&q, std::max<size_t>(P.rec_ntri.size() * sizeof(double), 16)) != cudaSuccess ||
+            cudaMalloc(&q2, std::max<size_t>(size_t(P.max_chunks * epi_nlm) * sizeof(double), 16)) != cudaSuccess) {
             cudaGetLastError();
+            if (q) cudaFree(q);
             return fail(BISP_OUT_OF_MEMORY, "device memory for the denominators");
         }
         d_nt = static_cast<double *>(q);
+        d_epi = static_cast<double *>(q2);
         cudaError_t e = cudaMemcpyAsync(d_nt, P.rec_ntri.data(), P.rec_ntri.size() * sizeof(double),
                                         cudaMemcpyHostToDevice, s);
         for (const View &v : P.views)
-            if (e == cudaSuccess)
-                e = launch_epilogue<double>(1, p->d_rec, p->d_bin_start + v.bs_off, v.n_bins, d_nt, v.l_lo, v.l_hi,
-                                            nullptr, 1.0, p->d_den + v.out_off, Batch{}, s);
+            if (e == cudaSuccess) {
+                const EpiArgs ea{p->d_rec, p->d_chunk_lo + v.chunk_off, p->d_chunk_hi + v.chunk_off, v.n_chunks,
+                                 p->d_bin_chunk + v.bc_off, v.n_bins, d_epi, 0};
+                e = launch_epilogue<double>(1, ea, d_nt, v.l_lo, v.l_hi, nullptr, 1.0, p->d_den + v.out_off,
+                                            Batch{}, s);
+            }
         p->h_den.resize(size_t(P.n_out));
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(p->h_den.data(), p->d_den, p->h_den.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(d_nt);
+        cudaFree(d_epi);
         if (e != cudaSuccess) return fail(BISP_CUDA_ERROR, std::string("denominators: ") + cudaGetErrorString(e));
         std::vector<double>().swap(P.rec_ntri);
     }
@@ -626,6 +640,7 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     p->off_part = o; o = align256(o + size_t(P.n_partials) * sizeof(double));
     p->off_S = o; o = align256(o + size_t(P.n_combos) * sizeof(double));
     p->off_status = o; o = align256(o + sizeof(int));
+    p->off_epi = o; o = align256(o + size_t(P.max_chunks * epi_nlm) * sizeof(double));
     p->region_bytes = o;
     CK(cudaStreamSynchronize(s));
     return desc->precision == BISP_PREC_FP64 ? autotune_transforms<double>(p, s) : autotune_transforms<float>(p, s);
@@ -715,11 +730,13 @@ int run_estimate(bisp_plan *p, const R *delta, int batch, unsigned char *ws, dou
         CK(launch_reduce_partials<RA>(p->d_groups, int64_t(P.groups.size()), part, ng, Ssum, region, s));
     }
     {   // binning and the ratio of Eq. bs_lm2_1
-        StageMark m(p, BISP_STAGE_BIN, int(P.views.size()), s);
-        for (const View &v : P.views)
-            CK(launch_epilogue<W>(0, p->d_rec, p->d_bin_start + v.bs_off, v.n_bins, Ssum, v.l_lo, v.l_hi,
-                                  p->d_den + v.out_off, 1.0 / (P.volume * double(ng2)), B + v.out_off, to_out, s,
-                                  p->precision != BISP_PREC_FP64));
+        StageMark m(p, BISP_STAGE_BIN, int(2 * P.views.size()), s);
+        for (const View &v : P.views) {
+            const EpiArgs ea{p->d_rec, p->d_chunk_lo + v.chunk_off, p->d_chunk_hi + v.chunk_off, v.n_chunks,
+                             p->d_bin_chunk + v.bc_off, v.n_bins, reinterpret_cast<double *>(ws + p->off_epi), fs};
+            CK(launch_epilogue<W>(0, ea, Ssum, v.l_lo, v.l_hi, p->d_den + v.out_off, 1.0 / (P.volume * double(ng2)),
+                                  B + v.out_off, to_out, s, p->precision != BISP_PREC_FP64));
+        }
     }
     p->last_field = batch - 1;
     return BISP_OK;

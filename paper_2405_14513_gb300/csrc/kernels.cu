@@ -574,20 +574,20 @@ __constant__ double c_rec[2][9][9];
 // nlm_out = that count per bin, for out and den alike.
 template <typename W, typename Y, int LMAX>
 __global__ void __launch_bounds__(256)
-k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ bin_start, int64_t nbins,
-           const double *__restrict__ value, const double *__restrict__ den, double norm,
-           double *__restrict__ out, int64_t fs_in, int64_t fs_out, int lm_lo, int nlm_out)
+k_epi_part(int mode, const Record *__restrict__ rec, const int64_t *__restrict__ chunk_lo,
+           const int64_t *__restrict__ chunk_hi, int64_t nchunks, const double *__restrict__ value,
+           double *__restrict__ partial, int64_t fs_in, int64_t fs_part)
 {
     value = field_ptr(value, fs_in);
-    out = field_ptr(out, fs_out);
+    partial = field_ptr(partial, fs_part);
     constexpr int NLM = (LMAX / 2 + 1) * (LMAX / 2 + 1);
-    const int64_t b = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t ch = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (b >= nbins) return;   // whole warps leave together
+    if (ch >= nchunks) return;   // whole warps leave together
     W acc[NLM];
 #pragma unroll
     for (int i = 0; i < NLM; ++i) acc[i] = W(0);
-    const int64_t k0 = bin_start[b], k1 = bin_start[b + 1];
+    const int64_t k0 = chunk_lo[ch], k1 = chunk_hi[ch];
     for (int64_t k = k0 + lane; k < k1; k += 32) {
         const Record R = rec[k];
         const Y x = Y(R.pz), c = Y(R.cphi);
@@ -630,16 +630,35 @@ k_epilogue(int mode, const Record *__restrict__ rec, const int64_t *__restrict__
     for (int i = 0; i < NLM; ++i) {
         W v = acc[i];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0 && i >= lm_lo) {
-            const int64_t o = b * nlm_out + (i - lm_lo);
-            if (mode == 0) {
-                int l = 0;
-                while ((l / 2 + 1) * (l / 2 + 1) <= i) l += 2;
-                const double d = den[o];
-                out[o] = d > 0.0 ? c_pref[l] * double(v) * norm / d : __longlong_as_double(0x7ff8000000000000LL);
-            } else {
-                out[o] = double(v);
-            }
+        if (lane == 0) partial[ch * NLM + i] = double(v);
+    }
+}
+
+// One thread per bin: its chunks' partial sums in chunk order, then (mode
+// 0) the ratio of Eq. bs_lm2_1 or (mode 1) the sum itself.
+template <int LMAX>
+__global__ void __launch_bounds__(256)
+k_epi_fin(int mode, const int64_t *__restrict__ bin_chunk, int64_t nbins, const double *__restrict__ partial,
+          const double *__restrict__ den, double norm, double *__restrict__ out, int64_t fs_part, int64_t fs_out,
+          int lm_lo, int nlm_out)
+{
+    partial = field_ptr(partial, fs_part);
+    out = field_ptr(out, fs_out);
+    constexpr int NLM = (LMAX / 2 + 1) * (LMAX / 2 + 1);
+    const int64_t b = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (b >= nbins) return;
+    const int64_t c0 = bin_chunk[b], c1 = bin_chunk[b + 1];
+    for (int i = lm_lo; i < NLM; ++i) {
+        double v = 0.0;
+        for (int64_t ch = c0; ch < c1; ++ch) v += partial[ch * NLM + i];
+        const int64_t o = b * nlm_out + (i - lm_lo);
+        if (mode == 0) {
+            int l = 0;
+            while ((l / 2 + 1) * (l / 2 + 1) <= i) l += 2;
+            const double d = den[o];
+            out[o] = d > 0.0 ? c_pref[l] * v * norm / d : __longlong_as_double(0x7ff8000000000000LL);
+        } else {
+            out[o] = v;
         }
     }
 }
@@ -810,35 +829,42 @@ cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const d
     return cudaGetLastError();
 }
 
-template <typename W, typename Y>
-cudaError_t epilogue_lmax(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins, const double *value,
-                          int l_lo, int l_hi, const double *den, double norm, double *out, const Batch &fb,
-                          cudaStream_t s)
+template <typename W, typename Y, int LMAX>
+cudaError_t epilogue_l(int mode, const EpiArgs &e, const double *value, const double *den, double norm, double *out,
+                       const Batch &fb, int lo, int n, cudaStream_t s)
 {
-    const dim3 grid(unsigned((nbins * 32 + 255) / 256), fb.nf);
-    const int64_t fi = fb.fs_in, fo = fb.fs_out;
-    const int lo = (l_lo / 2) * (l_lo / 2), n = (l_hi / 2 + 1) * (l_hi / 2 + 1) - lo;
-    switch (l_hi) {
-    case 0: k_epilogue<W, Y, 0><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
-    case 2: k_epilogue<W, Y, 2><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
-    case 4: k_epilogue<W, Y, 4><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
-    case 6: k_epilogue<W, Y, 6><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
-    case 8: k_epilogue<W, Y, 8><<<grid, 256, 0, s>>>(mode, rec, bin_start, nbins, value, den, norm, out, fi, fo, lo, n); break;
-    default: return cudaErrorInvalidValue;
-    }
+    const dim3 g1(unsigned((e.nchunks * 32 + 255) / 256), fb.nf), g2(unsigned((e.nbins + 255) / 256), fb.nf);
+    if (e.nchunks > 0)
+        k_epi_part<W, Y, LMAX><<<g1, 256, 0, s>>>(mode, e.rec, e.chunk_lo, e.chunk_hi, e.nchunks, value, e.partial,
+                                                  fb.fs_in, e.fs_part);
+    k_epi_fin<LMAX><<<g2, 256, 0, s>>>(mode, e.bin_chunk, e.nbins, e.partial, den, norm, out, e.fs_part, fb.fs_out,
+                                       lo, n);
     return cudaGetLastError();
 }
 
-template <typename W>
-cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
-                            const double *value, int l_lo, int l_hi, const double *den, double norm, double *out,
-                            const Batch &fb, cudaStream_t s, bool fp32_weights)
+template <typename W, typename Y>
+cudaError_t epilogue_lmax(int mode, const EpiArgs &e, const double *value, int l_lo, int l_hi, const double *den,
+                          double norm, double *out, const Batch &fb, cudaStream_t s)
 {
-    if (nbins == 0) return cudaSuccess;
+    const int lo = (l_lo / 2) * (l_lo / 2), n = (l_hi / 2 + 1) * (l_hi / 2 + 1) - lo;
+    switch (l_hi) {
+    case 0: return epilogue_l<W, Y, 0>(mode, e, value, den, norm, out, fb, lo, n, s);
+    case 2: return epilogue_l<W, Y, 2>(mode, e, value, den, norm, out, fb, lo, n, s);
+    case 4: return epilogue_l<W, Y, 4>(mode, e, value, den, norm, out, fb, lo, n, s);
+    case 6: return epilogue_l<W, Y, 6>(mode, e, value, den, norm, out, fb, lo, n, s);
+    case 8: return epilogue_l<W, Y, 8>(mode, e, value, den, norm, out, fb, lo, n, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename W>
+cudaError_t launch_epilogue(int mode, const EpiArgs &e, const double *value, int l_lo, int l_hi, const double *den,
+                            double norm, double *out, const Batch &fb, cudaStream_t s, bool fp32_weights)
+{
+    if (e.nbins == 0) return cudaSuccess;
     if (l_lo < 0 || l_lo > l_hi || (l_lo & 1)) return cudaErrorInvalidValue;
-    if (fp32_weights)
-        return epilogue_lmax<W, float>(mode, rec, bin_start, nbins, value, l_lo, l_hi, den, norm, out, fb, s);
-    return epilogue_lmax<W, W>(mode, rec, bin_start, nbins, value, l_lo, l_hi, den, norm, out, fb, s);
+    if (fp32_weights) return epilogue_lmax<W, float>(mode, e, value, l_lo, l_hi, den, norm, out, fb, s);
+    return epilogue_lmax<W, W>(mode, e, value, l_lo, l_hi, den, norm, out, fb, s);
 }
 
 // Every kernel that takes more than 48 KB of dynamic shared memory is
@@ -919,9 +945,9 @@ template cudaError_t launch_step2<double>(const StepIIArgs &, const double2 *, c
                                           cudaStream_t);
 template cudaError_t launch_reduce_partials<float>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
 template cudaError_t launch_reduce_partials<double>(const Group *, int64_t, const double *, int, double *, const Batch &, cudaStream_t);
-template cudaError_t launch_epilogue<float>(int, const Record *, const int64_t *, int64_t, const double *, int, int,
-                                            const double *, double, double *, const Batch &, cudaStream_t, bool);
-template cudaError_t launch_epilogue<double>(int, const Record *, const int64_t *, int64_t, const double *, int, int,
-                                             const double *, double, double *, const Batch &, cudaStream_t, bool);
+template cudaError_t launch_epilogue<float>(int, const EpiArgs &, const double *, int, int, const double *, double,
+                                            double *, const Batch &, cudaStream_t, bool);
+template cudaError_t launch_epilogue<double>(int, const EpiArgs &, const double *, int, int, const double *, double,
+                                             double *, const Batch &, cudaStream_t, bool);
 
 }  // namespace bisp

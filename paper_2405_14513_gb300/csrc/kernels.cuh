@@ -149,10 +149,21 @@ cudaError_t launch_reduce_partials(const Group *groups, int64_t ngroups, const d
 // (out and den: [nbins][moments of those l]).  mode 0: B = sqrt((2l+1)/4pi)
 // num / (V N_g^2 den) from S and den; mode 1: den from the triangle counts.
 // fp32_weights: the Y_lm of each record in FP32 (sums stay in W).
+// The records are walked in chunks of one bin each (one warp per chunk, FP64
+// partial sums per moment in `partial` [nchunks][moments of l <= l_hi]),
+// then each bin adds its chunks in order (one thread per bin).
+struct EpiArgs {
+    const Record *rec;
+    const int64_t *chunk_lo, *chunk_hi;   // record range of each chunk
+    int64_t nchunks;
+    const int64_t *bin_chunk;             // [nbins + 1]: first chunk of each bin
+    int64_t nbins;
+    double *partial;                      // field 0's partial sums
+    int64_t fs_part;                      // bytes between the fields' partial sums
+};
 template <typename W>
-cudaError_t launch_epilogue(int mode, const Record *rec, const int64_t *bin_start, int64_t nbins,
-                            const double *value, int l_lo, int l_hi, const double *den, double norm,
-                            double *out, const Batch &fb, cudaStream_t s, bool fp32_weights = false);
+cudaError_t launch_epilogue(int mode, const EpiArgs &e, const double *value, int l_lo, int l_hi, const double *den,
+                            double norm, double *out, const Batch &fb, cudaStream_t s, bool fp32_weights = false);
 
 // Y_lm normalisations nlm[l][m] and the prefactors sqrt((2l+1)/(4 pi)).
 cudaError_t set_ylm_constants(const double nlm[9][9], const double pref[9], cudaStream_t s);

@@ -783,6 +783,29 @@ void sort_records(HostPlan &P)
     }
     std::vector<Record>().swap(P.records_s);
     std::vector<double>().swap(P.ntri_s);
+    // binning chunks: each bin's records in runs of at most kBinChunk, so no
+    // warp of the binning walks a whole large bin alone
+    P.chunk_lo.clear();
+    P.chunk_hi.clear();
+    P.bin_chunk.assign(total_bs, 0);
+    P.max_chunks = 0;
+    int64_t bc = 0;
+    for (View &v : P.views) {
+        const int64_t *bs = P.bin_start.data() + v.bs_off;
+        v.chunk_off = int64_t(P.chunk_lo.size());
+        v.bc_off = bc;
+        for (int64_t b = 0; b < v.n_bins; ++b) {
+            P.bin_chunk[bc + b] = int64_t(P.chunk_lo.size()) - v.chunk_off;
+            for (int64_t k = bs[b]; k < bs[b + 1]; k += kBinChunk) {
+                P.chunk_lo.push_back(k);
+                P.chunk_hi.push_back(std::min(k + kBinChunk, bs[b + 1]));
+            }
+        }
+        v.n_chunks = int64_t(P.chunk_lo.size()) - v.chunk_off;
+        P.bin_chunk[bc + v.n_bins] = v.n_chunks;
+        bc += v.n_bins + 1;
+        P.max_chunks = std::max(P.max_chunks, v.n_chunks);
+    }
 }
 
 int unit_classes(const HostPlan &P, const int64_t **class_begin)

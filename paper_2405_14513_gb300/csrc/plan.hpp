@@ -164,11 +164,17 @@ struct Record {
 // bin_start at bs_off of the plan's bin_start array (absolute record
 // indices).  One view (every l on the caller's n_mu x n_t) unless per-l
 // bins are asked for; then consecutive l with the same grid share a view.
+// The binning runs over chunks of at most kBinChunk records of one bin (a
+// bin's records cut in order), chunk_off .. chunk_off + n_chunks - 1 of the
+// plan's chunk arrays, and bin b's chunks are bin_chunk[bc_off + b] ..
+// bin_chunk[bc_off + b + 1] - 1.
 struct View {
     int l_lo = 0, l_hi = 0, n_mu = 1, n_t = 1;
     int lm_lo = 0, n_lm = 1;           // first moment index (l_lo/2)^2, moments in the view
     int64_t n_bins = 0, out_off = 0, rec_off = 0, bs_off = 0;
+    int64_t chunk_off = 0, n_chunks = 0, bc_off = 0;
 };
+constexpr int64_t kBinChunk = 2048;
 
 struct Level {
     int lev = 0;               // index into Rings::grid
@@ -221,6 +227,9 @@ struct HostPlan {
     std::vector<Record> records;
     std::vector<double> rec_ntri;
     std::vector<int64_t> bin_start;     // per view: n_bins + 1 absolute record indices
+    std::vector<int64_t> chunk_lo, chunk_hi;   // record ranges of the binning chunks (all views)
+    std::vector<int64_t> bin_chunk;     // per view: n_bins + 1 chunk indices (relative to chunk_off)
+    int64_t max_chunks = 0;             // largest n_chunks of a view
 
     // D store: offset (in complex elements) of field (level, plane, ring),
     // -1 where not stored; [kMaxLevels][nz+1][kMaxRings]
