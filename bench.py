@@ -13,9 +13,14 @@ A k^-2, sigma_G = 0.1, f_NG = 0.5, Kaiser beta = 0.5).
 
 One step = one full estimate of one field (forward transform, Step I,
 Step II, binning).  The metric is output (k1, mu, t) bins per second, each
-bin carrying all 16 moments ("configs/s").  Each rank estimates its own
-field (independent problems, no collective in the data path): value is
-(ranks x bins) / max-over-ranks time, "scaling": "weak".
+bin carrying all 16 moments ("configs/s"; the line also gives the rate of
+populated bins).  On N > 1 GPUs (one rank each; started by this script when
+no launcher did) the default splits one field's Step II over the ranks with
+one sum all-reduce of the output ("scaling": "strong"); --split replicas
+gives each rank its own field instead (no collective, "scaling": "weak").
+At N = 1 the 512^3 line also carries the batched-mock (c4) and served (c5)
+results, the per-moment error against the stored FP64 oracle result, and
+the CPU oracle baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--precision P]
 
