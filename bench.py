@@ -177,7 +177,7 @@ STEP2_SOURCE = {
 
 def _traffic(ng, precision):
     """DRAM bytes of Step II per estimate from the committed ncu summary, if
-    it was taken at this grid size on the kernel source as it is now.
+    one was taken at this grid size on the kernel source as it is now.
     Returns (bytes, how) or (None, why)."""
     p = os.path.join(ROOT, "profiles", f"step2_dram_{precision}.json")
     try:
@@ -185,12 +185,13 @@ def _traffic(ng, precision):
             d = json.load(fh)
         if d.get("kernel_digest") != _kernel_digest(precision):
             return None, "the kernel changed since the DRAM capture"
-        if int(d["n_g"]) == ng:
-            return float(d["bytes_per_estimate"]), f"ncu capture at {ng}^3 ({d.get('source', '')})"
-        # a smaller grid is not scaled: its L2 hit rate differs (the D store
-        # of 256^3 is 1.8 GB, that of 512^3 17.9 GB)
+        for c in d["captures"]:
+            if int(c["n_g"]) == ng:
+                return float(c["bytes_per_estimate"]), f"ncu capture at {ng}^3 ({c.get('source', '')})"
+        # another grid size is not scaled: its L2 hit rate differs (the D
+        # store of 256^3 is 1.8 GB, that of 512^3 17.9 GB)
         return None, f"no capture at {ng}^3"
-    except (OSError, ValueError, KeyError):
+    except (OSError, ValueError, KeyError, TypeError):
         return None, "no capture"
 
 
@@ -498,9 +499,11 @@ def run_ours(args):
         roof = {"kernel": "k_step2 (Step II triple sums, FP32 FMA)", "bound": "alu",
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2070 MHz (nominal max clock)"}
     traffic, traffic_how = _traffic(ng, args.precision)
+    n2 = st_n["step2"] / args.steps          # Step-II launches per estimate; traffic is per launch, averaged
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": traffic, "traffic_source": traffic_how, "flops_per_estimate": flops["step2"],
-                 "ms_per_estimate": s2_ms, "launches_per_estimate": st_n["step2"] / args.steps})
+                 "traffic": None if traffic is None else traffic / n2,
+                 "traffic_per_estimate": traffic, "traffic_source": traffic_how,
+                 "flops_per_estimate": flops["step2"], "ms_per_estimate": s2_ms, "launches_per_estimate": n2})
     # Step I (HBM-bound transforms): algorithmic bytes = the D store written
     # once + the kept planes of Delta read once, over its own event time
     bf16_, hbm, src_ = _peaks()
