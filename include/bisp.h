@@ -252,9 +252,12 @@ int estimator_workspace_status(const bisp_plan *plan, const void *workspace, int
 /* Polls after which the tensor-core Step II's waits on its producer, compute
  * and MMA-issue stages give up (spins >= 1; 0 restores the default, 2^22).
  * The wait for the block's own MMAs before it frees its tensor memory keeps
- * the full bound.  A host-side knob for exercising the give-up path (a block
- * that gives up writes NaN sums and sets the workspace status); it applies
- * to later estimates of the plan.  (The paper has no counterpart.) */
+ * the full bound.  A poll may suspend the waiting thread for a while before
+ * it reports; below 64 polls each poll reports at once instead, so a small
+ * limit really cuts the waits short.  A host-side knob for exercising the
+ * give-up path (a block that gives up writes NaN sums and sets the workspace
+ * status); it applies to later estimates of the plan.  (The paper has no
+ * counterpart.) */
 int estimator_set_wait_limit(bisp_plan *plan, int spins);
 
 /* Release the plan and everything it owns (NULL is a no-op).  The caller

@@ -87,12 +87,16 @@ constexpr int kTcSlotBytes = kTcTX * 8 + 16;   // one staged field row (padded)
 constexpr int kTcMinStages = 3;
 constexpr int kTcMaxStages = 8;
 constexpr size_t kTcSmem = 110 * 1024;         // dynamic shared memory of a block (two per SM)
+// Buffers of a stage's A and B operands: three for NC <= 32 (3 x 64 columns
+// of A and two accumulators of NC columns fit the 256 tensor-memory columns
+// of a block), two otherwise.
+BISP_HD constexpr int tc_abuf(int ncol) { return ncol <= 32 ? 3 : 2; }
 // Shared memory of a tcgen05 block other than its stage ring: B high and
-// low parts (two buffers each), field offsets, barriers; a multiple of 128
-// bytes, so that the ring that follows is aligned for 16-byte copies.
+// low parts (tc_abuf buffers each), field offsets, barriers; a multiple of
+// 128 bytes, so that the ring that follows is aligned for 16-byte copies.
 BISP_HD inline size_t tc_fixed_smem(int ncol, int nslot)
 {
-    return size_t(4) * ncol * kTcTX * 8 + ((8 * size_t(nslot + ncol) + 256 + 127) & ~size_t(127));
+    return size_t(2 * tc_abuf(ncol)) * ncol * kTcTX * 8 + ((8 * size_t(nslot + ncol) + 256 + 127) & ~size_t(127));
 }
 // Stages of the ring for a tile (0 if fewer than kTcMinStages fit): each
 // stage holds the tile's nslot + ncol fields and one zero row.

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kTX = kTcTX;                   // grid points per stage (K = 32)
 constexpr int kSlotBytes = kTcSlotBytes;
-constexpr uint32_t kTmemCols = 256;          // A[2] (hi 32 + lo 32 columns each), then the accumulators
+constexpr uint32_t kTmemCols = 256;          // A[tc_abuf] (hi 32 + lo 32 columns each), then the accumulators
 constexpr int kDrainSpins = kDefaultWaitSpins;  // bound of the wait for the block's own MMAs
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -64,11 +64,23 @@ __host__ __device__ constexpr uint32_t idesc_tf32()
     return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(128 >> 4) << 24);
 }
 
+// One MMA, issued by one elected lane of a converged warp whose lanes all
+// hold the same operands.  Issued this way the operands stay warp-uniform,
+// and a stage's twelve MMAs issue in ~15 cycles each; issued from a single
+// lane (inside a lane test) they took ~48.
 __device__ __forceinline__ void mma_tf32(uint32_t d, uint32_t a, uint64_t b, uint32_t id, uint32_t acc)
 {
-    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+    asm volatile("{\n.reg .pred p, e;\nsetp.ne.b32 p, %4, 0;\nelect.sync _|e, 0xffffffff;\n"
+                 "@e tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
                  ::"r"(d), "r"(a), "l"(b), "r"(id), "r"(acc) : "memory");
+}
+
+// tcgen05.commit of the warp's MMAs to mbarrier m, by one elected lane
+__device__ __forceinline__ void mma_commit(uint32_t m)
+{
+    asm volatile("{\n.reg .pred e;\nelect.sync _|e, 0xffffffff;\n"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n"
+                 ::"r"(m) : "memory");
 }
 
 // -hi(x): x with its 13 low mantissa bits cleared, negated (one logical operation)
@@ -125,34 +137,42 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 }
 
 // One block per unit (tile, x chunk), warp-specialised:
-//   warps 0-7  form A and write B's high and low parts; warps w and w + 4
-//              share tensor-memory lanes 32 (w % 4) .. (the tile's rows,
-//              one per lane): warp w forms grid points 0-7 of a stage and
-//              adds accumulator columns 0 .. NC/2 - 1 into FP32 registers,
-//              warp w + 4 points 8-15 and columns NC/2 .. NC - 1;
-//   warp 8     (one thread) issues the 12 MMAs of a stage into the
-//              accumulator of its buffer b (tensor-memory columns
-//              128 + 64 b).  Accumulators are double-buffered, so the MMAs
-//              of stage s wait only for stage s - 2's read.  (A second
-//              issuer with an accumulator of its own was slower: the compute
-//              warps, not the MMA issue, set the pace, and a second
-//              accumulator doubles their reads);
+//   warps 0-7  form A and write B's high and low parts into buffer
+//              st % NA of stage st (NA = tc_abuf(NC): 3 for NC <= 32, else
+//              2; A in tensor-memory columns 64 a .. 64 a + 63); warps w and
+//              w + 4 share tensor-memory lanes 32 (w % 4) .. (the tile's
+//              rows, one per lane): warp w forms grid points 0-7 of a stage
+//              and adds accumulator columns 0 .. NC/2 - 1 into FP32
+//              registers, warp w + 4 points 8-15 and columns NC/2 .. NC - 1,
+//              reading the accumulators of stage st - (NA - 1) after forming
+//              stage st;
+//   warp 8     issues the 12 MMAs of a stage (one elected lane) into
+//              accumulator buffer st & 1 (tensor-memory columns from 64 NA,
+//              NC apart with three A buffers, 64 apart with two).  The MMAs
+//              of stage st wait for A(st) and for the read of stage st - 2's
+//              accumulators.  (A second issuer with an accumulator of its
+//              own was slower: a second accumulator doubles the compute
+//              warps' reads);
 //   warps 9-10 stage the fields of each stage in shared memory (cp.async,
 //              a ring of 3 to 8 stages).
 // mbarriers (phase k of a barrier = its k-th use):
 //   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
 //   empty[q]  ring buffer q has been read             (256 compute arrivals)
-//   aready[b] A and B (high, low) of buffer b written (256 compute arrivals)
-//   mdone[b]  the MMAs into buffer b are done         (commit)
-//   dfree[b]  accumulators of buffer b have been read (256 compute arrivals)
+//   aready[a] A and B (high, low) of buffer a written (256 compute arrivals)
+//   mdone[b]  the MMAs into accumulator b are done    (commit)
+//   dfree[b]  accumulator b has been read             (256 compute arrivals)
 //   drain     every MMA the block issued is done      (commit; before the
 //             tensor memory is freed, also when the block gives up early)
+// A barrier's next phase cannot complete before its waiters have seen the
+// current one: A(st + NA) is formed only after the accumulators of stage st
+// were read, which waited for mdone of stage st, and the MMAs of stage
+// st + 2 wait for that read.
 constexpr int kThreads = 352;
 constexpr int kCompute = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
-    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[2], mdone[2], dfree[2], drain;
+    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[3], mdone[2], dfree[2], drain;
     uint32_t tmem;
     int abort;
 };
@@ -169,14 +189,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *m)
 }
 
 // Bounded wait for phase `parity` of m; gives up (false) when the block is
-// aborting or after `spins` polls, and then raises the abort flag.
+// aborting or after `spins` polls, and then raises the abort flag.  A poll
+// is a try_wait, which may suspend the thread for a while before it reports;
+// under kTestPolls polls (a limit set to exercise the give-up path) it is a
+// test_wait, which reports at once, so that such a limit really cuts the
+// wait short.
+constexpr int kTestPolls = 64;
 __device__ __forceinline__ bool mbar_wait_abort(uint64_t *m, uint32_t parity, volatile int *abort, int spins)
 {
     const uint32_t a = su32(m);
+    const bool test = spins < kTestPolls;
     for (int i = 0; i < spins; ++i) {
         uint32_t ok;
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        if (test)
+            asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(ok) : "r"(a), "r"(parity) : "memory");
+        else
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                         : "=r"(ok) : "r"(a), "r"(parity) : "memory");
         if (ok) return true;
         if (*abort) return false;
     }
@@ -243,9 +273,15 @@ struct CompArgs {
     int rowb, nslot, S, nstage, spins, t, half, s1, s2;
 };
 
+// Tensor-memory column of accumulator buffer 0 and the distance to buffer 1
+template <int NC> __device__ constexpr uint32_t acc_col0() { return 64u * tc_abuf(NC); }
+template <int NC> __device__ constexpr uint32_t acc_step() { return tc_abuf(NC) == 3 ? uint32_t(NC) : 64u; }
+
 // The stage loop of one compute thread: form A (its row's 8 points of the
-// stage) and its share of B, then add the accumulators of the stage before.
-// Returns false if a wait gave up.  B piece p (grid points 2p, 2p + 1) of
+// stage) and its share of B into buffer st % NA, then add the accumulators
+// of stage st - (NA - 1): with three buffers the MMAs of a stage have the
+// whole next stage to finish before their sums are read.  Returns false if
+// a wait gave up.  B piece p (grid points 2p, 2p + 1) of
 // column c goes to core matrix (K block p, rows 8 (c / 8) ..), row c % 8;
 // this thread's pieces are i = t and t + 256 (i = p NC + c), fixed for the
 // tile, so their offsets are computed once.
@@ -256,6 +292,7 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     constexpr int NB = NC / 8;
     constexpr int BB = NC * kTX * 8;
     constexpr int NP = (NC * 8 + kCompute - 1) / kCompute;    // B pieces per thread (at most 2)
+    constexpr int NA = tc_abuf(NC), LAG = NA - 1;
     TcSync *sy = ca.sy;
     int src[NP], dst[NP];
 #pragma unroll
@@ -272,20 +309,20 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     int q = 0;                                   // ring buffer of stage st
     uint32_t ph = 0;                             // its phase: (st / S) & 1
     const unsigned char *sq = ca.sS;             // ring buffer q
-    for (int st = 0; st <= ca.nstage; ++st) {
+    int ia = 0;                                  // A / B buffer of stage st: st % NA
+    for (int st = 0; st < ca.nstage + LAG; ++st) {
         if (st < ca.nstage) {
-            const int b = st & 1;
             ok = mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins);
             if (!ok) break;
-            form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * b, ca.half);
-            // B, high and low parts, in the canonical layout.  Buffer b was
-            // last read by the MMAs of stage st - 2, complete: their
+            form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * ia, ca.half);
+            // B, high and low parts, in the canonical layout.  Buffer ia was
+            // last read by the MMAs of stage st - NA, complete: their
             // accumulators were read at stage st - 1.
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
                 if (src[k] < 0) continue;
                 const float4 v = *reinterpret_cast<const float4 *>(sq + src[k]);
-                const int o = b * BB + dst[k];
+                const int o = ia * BB + dst[k];
                 *reinterpret_cast<float4 *>(ca.sHi + o) = v;
                 uint4 l;
                 lo2(v.x, v.y, l.x, l.y);
@@ -303,16 +340,17 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
             asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            mbar_arrive(&sy->aready[b]);
+            mbar_arrive(&sy->aready[ia]);
+            if (++ia == NA) ia = 0;
         }
-        if (st > 0) {
-            // accumulators of stage st - 1 (buffer b)
-            const int b = (st - 1) & 1;
-            const uint32_t par = uint32_t((st - 1) >> 1) & 1;
+        if (st >= LAG) {
+            // accumulators of stage st - LAG (buffer b)
+            const int s = st - LAG, b = s & 1;
+            const uint32_t par = uint32_t(s >> 1) & 1;
             ok = mbar_wait_abort(&sy->mdone[b], par, ca.abort, ca.spins);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            add_accumulator<NH>(ca.tlane + 128 + 64 * b + NH * ca.half, acc);
+            add_accumulator<NH>(ca.tlane + acc_col0<NC>() + acc_step<NC>() * b + NH * ca.half, acc);
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             mbar_arrive(&sy->dfree[b]);
         }
@@ -332,6 +370,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     constexpr uint32_t LBO = NB * 128;           // next core matrix along K
     constexpr uint32_t SBO = 128;                // next 8 rows of B
     constexpr int BB = NC * kTX * 8;             // bytes of one stage of B
+    constexpr int NA = tc_abuf(NC);              // A / B buffers
     constexpr uint32_t ID = idesc_tf32<NC>();
     extern __shared__ __align__(1024) unsigned char smem[];
 
@@ -346,13 +385,13 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     const int nslot = T.nslot, nf = nslot + NC;
     const int S = tc_stages(NC, nslot);          // ring depth (>= 3; the plan checked)
     const int rowb = (nf + 1) * kSlotBytes;      // one ring buffer: nf fields and a zero row
-    // shared memory: B high and low parts [2][BB] each (canonical layout),
+    // shared memory: B high and low parts [NA][BB] each (canonical layout),
     // field offsets [nf], barriers, ring [S][nf + 1][kSlotBytes] (D1 / D2
     // slots, the B window, a zero row)
     unsigned char *sHi = smem;
-    unsigned char *sLo = smem + 2 * BB;
-    int64_t *offs = reinterpret_cast<int64_t *>(smem + 4 * BB);
-    TcSync *sy = reinterpret_cast<TcSync *>(smem + 4 * BB + 8 * size_t(nf));
+    unsigned char *sLo = smem + NA * BB;
+    int64_t *offs = reinterpret_cast<int64_t *>(smem + 2 * NA * BB);
+    TcSync *sy = reinterpret_cast<TcSync *>(smem + 2 * NA * BB + 8 * size_t(nf));
     unsigned char *sS = smem + tc_fixed_smem(NC, nslot);
 
     for (int f = t; f < nf; f += kThreads) {
@@ -371,8 +410,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             mbar_init(&sy->full[q], 64);
             mbar_init(&sy->empty[q], kCompute);
         }
+        for (int b = 0; b < NA; ++b) mbar_init(&sy->aready[b], kCompute);
         for (int b = 0; b < 2; ++b) {
-            mbar_init(&sy->aready[b], kCompute);
             mbar_init(&sy->mdone[b], 1);
             mbar_init(&sy->dfree[b], kCompute);
         }
@@ -410,6 +449,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         // 16-element units: every stored field starts at a multiple of 16)
         // are held in registers
         const int pl = t - 288, p = pl & 7, f0 = pl >> 3;
+        // (all kProdFields copies are issued under a predicate: a loop
+        // bound by the fields that exist was 6% slower)
         uint32_t o16[kProdFields];
 #pragma unroll
         for (int k = 0; k < kProdFields; ++k) {
@@ -433,18 +474,24 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
         asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else if (warp == 8) {
         // MMA issue: high A x high B, low A x high B and high A x low B over
-        // the four k-steps of the stage
-        if (lane == 0) {
+        // the four k-steps of the stage.  The whole warp runs the loop (all
+        // lanes wait, one elected lane issues), so that its operands are
+        // warp-uniform; a lane's wait that gives up stops the warp.
+        {
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
+            int ia = 0;                                         // A / B buffer of stage st
+            uint32_t pa = 0;                                    // its phase: (st / NA) & 1
             for (int st = 0; st < nstage && ok; ++st) {
-                const int b = st & 1;
-                ok = mbar_wait_abort(&sy->aready[b], uint32_t(st >> 1) & 1, abort, spins);
+                const int b = st & 1;                           // accumulator buffer
+                ok = mbar_wait_abort(&sy->aready[ia], pa, abort, spins);
                 if (ok && st >= 2) ok = mbar_wait_abort(&sy->dfree[b], uint32_t((st - 2) >> 1) & 1, abort, spins);
+                ok = __all_sync(0xFFFFFFFFu, ok);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                const uint32_t a = tmem + 64 * b;
-                const uint32_t d = tmem + 128 + 64 * b;
-                const uint64_t bo = uint64_t(b * BB) >> 4;      // start-address field offset of buffer b
+                const uint32_t a = tmem + 64 * ia;
+                const uint32_t d = tmem + acc_col0<NC>() + acc_step<NC>() * b;
+                const uint64_t bo = uint64_t(ia * BB) >> 4;     // start-address field offset of buffer ia
+                if (++ia == NA) { ia = 0; pa ^= 1u; }
                 constexpr uint64_t kstep = (2 * LBO) >> 4;      // next k-step (two core matrices along K)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dh + bo + j * kstep, ID, j > 0);
@@ -452,12 +499,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
                 for (int j = 0; j < 4; ++j) mma_tf32(d, a + 32 + 8 * j, dh + bo + j * kstep, ID, 1);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_tf32(d, a + 8 * j, dl + bo + j * kstep, ID, 1);
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                             ::"r"(su32(&sy->mdone[b])) : "memory");
+                mma_commit(su32(&sy->mdone[b]));
             }
             // the MMAs issued so far finish before the tensor memory is freed
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
-                         ::"r"(su32(&sy->drain)) : "memory");
+            mma_commit(su32(&sy->drain));
             mbar_wait_bounded(&sy->drain, 0);
         }
         __syncwarp();

@@ -485,11 +485,12 @@ def test_mock_statistics_match_per_field_estimates():
 
 def test_tensor_core_waits_give_up_and_the_plan_recovers():
     """The tcgen05 Step II bounds every wait.  With the limit cut to one poll
-    (the producers' first copies cannot have landed by then), its blocks give
-    up: they write NaN sums, and the workspace status reports BISP_TIMEOUT for
-    that estimate only; every populated bin is then NaN.  With the default
-    limit restored, the next estimate on the same plan and workspace is the
-    normal one again, bit for bit, and reports success."""
+    (a poll that reports at once; the producers' first copies cannot have
+    landed by then), its blocks give up: they write NaN sums, and the
+    workspace status reports BISP_TIMEOUT for that estimate only; every
+    populated bin is then NaN.  With the default limit restored, the next
+    estimate on the same plan and workspace is the normal one again, bit for
+    bit, and reports success."""
     ng, L = 16, 1000.0
     edges = synth.default_k1_edges(ng, L, 3)
     field = torch.from_numpy(synth.make_field(ng, L, 2).astype(np.float32)).cuda()[None].contiguous()
