@@ -278,13 +278,15 @@ template <int NC> __device__ constexpr uint32_t acc_col0() { return 64u * tc_abu
 template <int NC> __device__ constexpr uint32_t acc_step() { return tc_abuf(NC) == 3 ? uint32_t(NC) : 64u; }
 
 // The stage loop of one compute thread: form A (its row's 8 points of the
-// stage) and its share of B into buffer st % NA, then add the accumulators
-// of stage st - (NA - 1): with three buffers the MMAs of a stage have the
-// whole next stage to finish before their sums are read.  Returns false if
-// a wait gave up.  B piece p (grid points 2p, 2p + 1) of
-// column c goes to core matrix (K block p, rows 8 (c / 8) ..), row c % 8;
-// this thread's pieces are i = t and t + 256 (i = p NC + c), fixed for the
-// tile, so their offsets are computed once.
+// stage) and its share of B into buffer st % NA, and add the accumulators of
+// stage st - (NA - 1).  With two buffers the sums of stage st - 1 are read
+// after forming stage st (the MMAs of st - 1 run meanwhile); with three, the
+// sums of stage st - 2 are read first, so that the MMAs of stage st (which
+// wait for that read) can start as soon as A(st) is written, and have the
+// whole next stage to finish.  Returns false if a wait gave up.  B piece p
+// (grid points 2p, 2p + 1) of column c goes to core matrix (K block p, rows
+// 8 (c / 8) ..), row c % 8; this thread's pieces are i = t and t + 256
+// (i = p NC + c), fixed for the tile, so their offsets are computed once.
 template <int NC, bool G1, bool G2, bool G3>
 __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC / 2])
 {
@@ -293,6 +295,7 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     constexpr int BB = NC * kTX * 8;
     constexpr int NP = (NC * 8 + kCompute - 1) / kCompute;    // B pieces per thread (at most 2)
     constexpr int NA = tc_abuf(NC), LAG = NA - 1;
+    constexpr bool READ_FIRST = NA == 3;
     TcSync *sy = ca.sy;
     int src[NP], dst[NP];
 #pragma unroll
@@ -305,57 +308,57 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     const int uoff = ca.s1 * kSlotBytes, voff = ca.s2 * kSlotBytes;
 #pragma unroll
     for (int c = 0; c < NH; ++c) acc[c] = 0.f;
-    bool ok = true;
     int q = 0;                                   // ring buffer of stage st
     uint32_t ph = 0;                             // its phase: (st / S) & 1
     const unsigned char *sq = ca.sS;             // ring buffer q
     int ia = 0;                                  // A / B buffer of stage st: st % NA
-    for (int st = 0; st < ca.nstage + LAG; ++st) {
-        if (st < ca.nstage) {
-            ok = mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins);
-            if (!ok) break;
-            form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * ia, ca.half);
-            // B, high and low parts, in the canonical layout.  Buffer ia was
-            // last read by the MMAs of stage st - NA, complete: their
-            // accumulators were read at stage st - 1.
+    // A and B of stage st into buffer ia (last read by the MMAs of stage
+    // st - NA, complete: their sums have been read)
+    auto form = [&](int st) -> bool {
+        if (!mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins)) return false;
+        form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * ia, ca.half);
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                if (src[k] < 0) continue;
-                const float4 v = *reinterpret_cast<const float4 *>(sq + src[k]);
-                const int o = ia * BB + dst[k];
-                *reinterpret_cast<float4 *>(ca.sHi + o) = v;
-                uint4 l;
-                lo2(v.x, v.y, l.x, l.y);
-                lo2(v.z, v.w, l.z, l.w);
-                *reinterpret_cast<uint4 *>(ca.sLo + o) = l;
-            }
-            mbar_arrive(&sy->empty[q]);
-            if (++q == ca.S) {
-                q = 0;
-                ph ^= 1u;
-                sq = ca.sS;
-            } else {
-                sq += ca.rowb;
-            }
-            asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            mbar_arrive(&sy->aready[ia]);
-            if (++ia == NA) ia = 0;
+        for (int k = 0; k < NP; ++k) {
+            if (src[k] < 0) continue;
+            const float4 v = *reinterpret_cast<const float4 *>(sq + src[k]);
+            const int o = ia * BB + dst[k];
+            *reinterpret_cast<float4 *>(ca.sHi + o) = v;
+            uint4 l;
+            lo2(v.x, v.y, l.x, l.y);
+            lo2(v.z, v.w, l.z, l.w);
+            *reinterpret_cast<uint4 *>(ca.sLo + o) = l;
         }
-        if (st >= LAG) {
-            // accumulators of stage st - LAG (buffer b)
-            const int s = st - LAG, b = s & 1;
-            const uint32_t par = uint32_t(s >> 1) & 1;
-            ok = mbar_wait_abort(&sy->mdone[b], par, ca.abort, ca.spins);
-            if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            add_accumulator<NH>(ca.tlane + acc_col0<NC>() + acc_step<NC>() * b + NH * ca.half, acc);
-            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-            mbar_arrive(&sy->dfree[b]);
+        mbar_arrive(&sy->empty[q]);
+        if (++q == ca.S) {
+            q = 0;
+            ph ^= 1u;
+            sq = ca.sS;
+        } else {
+            sq += ca.rowb;
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(&sy->aready[ia]);
+        if (++ia == NA) ia = 0;
+        return true;
+    };
+    // the accumulators of stage s (buffer s & 1)
+    auto read = [&](int s) -> bool {
+        const int b = s & 1;
+        if (!mbar_wait_abort(&sy->mdone[b], uint32_t(s >> 1) & 1, ca.abort, ca.spins)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        add_accumulator<NH>(ca.tlane + acc_col0<NC>() + acc_step<NC>() * b + NH * ca.half, acc);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        mbar_arrive(&sy->dfree[b]);
+        return true;
+    };
+    for (int st = 0; st < ca.nstage + LAG; ++st) {
+        if (READ_FIRST && st >= LAG && !read(st - LAG)) return false;
+        if (st < ca.nstage && !form(st)) return false;
+        if (!READ_FIRST && st >= LAG && !read(st - LAG)) return false;
     }
-    return ok;
+    return true;
 }
 
 // Two blocks per SM (sharing its 227 KB of shared memory and 512
