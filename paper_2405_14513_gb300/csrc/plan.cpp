@@ -207,7 +207,7 @@ void enumerate_pair(const HostPlan &P, int n1, int n2, PairOut &out)
 // tcgen05 tiles (see TcTile): the groups of each (grid, |n3|, signs of n1,
 // n2, n3) in order of n1, their rows by the centre of their r3 run, cut
 // greedily into tiles of at most 128 rows and a window of at most 64 r3
-// whose fields fit kTcMinStages stages of shared memory; then units (tile,
+// whose fields fit kTcMinRing ring buffers of shared memory; then units (tile,
 // x chunk) by class.
 // Requires the groups' partial-sum layout.  Marks the fields the tiles read.
 template <typename UsedFn>
@@ -253,7 +253,7 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
         T.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
         T.flags = cur_flags;
         if (cur_flags & 1) return "tcgen05 tiles need n1 >= 0";
-        if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows || tc_stages(T.ncol, T.nslot) == 0)
+        if (T.ncol > kTcMaxCols || T.nslot > kTcMaxSlots || T.nrow > kTcRows || tc_ring(T.ncol, T.nslot) == 0)
             return "tcgen05 tile limits";
         // rows (tensor-memory lanes) in order of their D1 field, then D2
         // field, and the staged fields numbered in that order: lanes of one
@@ -313,7 +313,7 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
                 num[f] = best + 8 * next[best]++;
                 top = std::max(top, num[f] + 1);
             }
-            if (top <= kTcMaxSlots && tc_stages(T.ncol, top) > 0) {
+            if (top <= kTcMaxSlots && tc_ring(T.ncol, top) > 0) {
                 std::vector<int32_t> sl(size_t(top), (0 << 8) | R.nr);   // ring nr: never stored
                 for (int f = 0; f < ns; ++f) sl[num[f]] = cur.slots[f];
                 cur.slots.swap(sl);
@@ -379,7 +379,7 @@ std::string build_tc(HostPlan &P, int64_t x_chunk, UsedFn &&U_)
                         const int ncol = ((hi - lo + 1 + 15) / 16) * 16;
                         const int ns = int(cur.slots.size()) + add;
                         if (int(cur.rows.size()) >= kTcRows || hi - lo + 1 > kTcMaxCols || ns > kTcMaxSlots ||
-                            tc_stages(ncol, ns) == 0) {
+                            tc_ring(ncol, ns) == 0) {
                             e = close();
                             if (!e.empty()) return e;
                         }

@@ -82,10 +82,11 @@ constexpr int kTcRows = 128;
 constexpr int kTcMaxCols = 64;
 constexpr int kTcMaxSlots = 250;      // distinct D1 / D2 fields staged by a tile
 constexpr int kTcClasses = 4;         // NC = 16 (class + 1)
-constexpr int kTcTX = 16;             // grid points of one pipeline stage
-constexpr int kTcSlotBytes = kTcTX * 8 + 16;   // one staged field row (padded)
-constexpr int kTcMinStages = 3;
-constexpr int kTcMaxStages = 8;
+constexpr int kTcTX = 16;             // grid points of one pipeline stage (one MMA step)
+constexpr int kTcRingTX = 2 * kTcTX;  // grid points of one ring buffer (two stages)
+constexpr int kTcSlotBytes = kTcRingTX * 8 + 16;   // one staged field row of a ring buffer (padded)
+constexpr int kTcMinRing = 2;         // ring buffers
+constexpr int kTcMaxRing = 4;
 constexpr size_t kTcSmem = 110 * 1024;         // dynamic shared memory of a block (two per SM)
 // Buffers of a stage's A and B operands: three for NC <= 32 (3 x 64 columns
 // of A and two accumulators of NC columns fit the 256 tensor-memory columns
@@ -98,15 +99,15 @@ BISP_HD inline size_t tc_fixed_smem(int ncol, int nslot)
 {
     return size_t(2 * tc_abuf(ncol)) * ncol * kTcTX * 8 + ((8 * size_t(nslot + ncol) + 256 + 127) & ~size_t(127));
 }
-// Stages of the ring for a tile (0 if fewer than kTcMinStages fit): each
-// stage holds the tile's nslot + ncol fields and one zero row.
-BISP_HD inline int tc_stages(int ncol, int nslot)
+// Buffers of the stage ring for a tile (0 if fewer than kTcMinRing fit):
+// each holds two stages of the tile's nslot + ncol fields and one zero row.
+BISP_HD inline int tc_ring(int ncol, int nslot)
 {
     const size_t fixed = tc_fixed_smem(ncol, nslot);
     if (fixed >= kTcSmem) return 0;
     const size_t per = size_t(nslot + ncol + 1) * kTcSlotBytes;
     const int n = int((kTcSmem - fixed) / per);
-    return n < kTcMinStages ? 0 : (n > kTcMaxStages ? kTcMaxStages : n);
+    return n < kTcMinRing ? 0 : (n > kTcMaxRing ? kTcMaxRing : n);
 }
 struct TcRow {
     int64_t p0;                // partial sum of (x chunk 0, first combination of the run)

@@ -36,7 +36,7 @@ namespace bisp {
 namespace {
 
 constexpr int kTX = kTcTX;                   // grid points per stage (K = 32)
-constexpr int kSlotBytes = kTcSlotBytes;
+constexpr int kSlotBytes = kTcSlotBytes;     // a field's row of a ring buffer: two stages (+ padding)
 constexpr uint32_t kTmemCols = 256;          // A[tc_abuf] (hi 32 + lo 32 columns each), then the accumulators
 constexpr int kDrainSpins = kDefaultWaitSpins;  // bound of the wait for the block's own MMAs
 
@@ -154,9 +154,10 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 //              own was slower: a second accumulator doubles the compute
 //              warps' reads);
 //   warps 9-10 stage the fields of each stage in shared memory (cp.async,
-//              a ring of 3 to 8 stages).
+//              a ring of 2 to 4 buffers of two stages each: 32 grid points
+//              a field row, waited for and released once per two stages).
 // mbarriers (phase k of a barrier = its k-th use):
-//   full[q]   stage data in ring buffer q landed      (64 producer arrivals)
+//   full[q]   the data of ring buffer q landed        (64 producer arrivals)
 //   empty[q]  ring buffer q has been read             (256 compute arrivals)
 //   aready[a] A and B (high, low) of buffer a written (256 compute arrivals)
 //   mdone[b]  the MMAs into accumulator b are done    (commit)
@@ -172,7 +173,7 @@ constexpr int kCompute = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
-    uint64_t full[kTcMaxStages], empty[kTcMaxStages], aready[3], mdone[2], dfree[2], drain;
+    uint64_t full[kTcMaxRing], empty[kTcMaxRing], aready[3], mdone[2], dfree[2], drain;
     uint32_t tmem;
     int abort;
 };
@@ -308,19 +309,22 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     const int uoff = ca.s1 * kSlotBytes, voff = ca.s2 * kSlotBytes;
 #pragma unroll
     for (int c = 0; c < NH; ++c) acc[c] = 0.f;
-    int q = 0;                                   // ring buffer of stage st
-    uint32_t ph = 0;                             // its phase: (st / S) & 1
+    int q = 0;                                   // ring buffer of stage st: (st / 2) % S
+    uint32_t ph = 0;                             // its phase: (st / 2S) & 1
     const unsigned char *sq = ca.sS;             // ring buffer q
     int ia = 0;                                  // A / B buffer of stage st: st % NA
-    // A and B of stage st into buffer ia (last read by the MMAs of stage
-    // st - NA, complete: their sums have been read)
+    // A and B of stage st (half st & 1 of ring buffer q) into buffer ia
+    // (last read by the MMAs of stage st - NA, complete: their sums have
+    // been read); the ring buffer is waited for at its first stage and
+    // released after its second (or the last stage)
     auto form = [&](int st) -> bool {
-        if (!mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins)) return false;
-        form_a<G1, G2, G3>(sq + uoff, sq + voff, ca.tlane + 64 * ia, ca.half);
+        const int h = (st & 1) * (kTX * 8);
+        if (h == 0 && !mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins)) return false;
+        form_a<G1, G2, G3>(sq + uoff + h, sq + voff + h, ca.tlane + 64 * ia, ca.half);
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
             if (src[k] < 0) continue;
-            const float4 v = *reinterpret_cast<const float4 *>(sq + src[k]);
+            const float4 v = *reinterpret_cast<const float4 *>(sq + src[k] + h);
             const int o = ia * BB + dst[k];
             *reinterpret_cast<float4 *>(ca.sHi + o) = v;
             uint4 l;
@@ -328,13 +332,15 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
             lo2(v.z, v.w, l.z, l.w);
             *reinterpret_cast<uint4 *>(ca.sLo + o) = l;
         }
-        mbar_arrive(&sy->empty[q]);
-        if (++q == ca.S) {
-            q = 0;
-            ph ^= 1u;
-            sq = ca.sS;
-        } else {
-            sq += ca.rowb;
+        if (h != 0 || st + 1 == ca.nstage) {
+            mbar_arrive(&sy->empty[q]);
+            if (++q == ca.S) {
+                q = 0;
+                ph ^= 1u;
+                sq = ca.sS;
+            } else {
+                sq += ca.rowb;
+            }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -386,10 +392,10 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     args.status = reinterpret_cast<int *>(reinterpret_cast<char *>(args.status) + int64_t(blockIdx.y) * args.fs);
     const int spins = args.wait_spins;
     const int nslot = T.nslot, nf = nslot + NC;
-    const int S = tc_stages(NC, nslot);          // ring depth (>= 3; the plan checked)
+    const int S = tc_ring(NC, nslot);            // ring buffers (>= 2; the plan checked)
     const int rowb = (nf + 1) * kSlotBytes;      // one ring buffer: nf fields and a zero row
     // shared memory: B high and low parts [NA][BB] each (canonical layout),
-    // field offsets [nf], barriers, ring [S][nf + 1][kSlotBytes] (D1 / D2
+    // field offsets [nf], barriers, ring [S][nf + 1][kSlotBytes] (two stages of D1 / D2
     // slots, the B window, a zero row)
     unsigned char *sHi = smem;
     unsigned char *sLo = smem + NA * BB;
@@ -429,8 +435,8 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     }
     __syncthreads();
     // fields that are not stored (past the last ring), and the zero row, read as zero
-    for (int i = t; i < S * (nf + 1) * 8; i += kThreads) {
-        const int q = i / ((nf + 1) * 8), rem = i - q * (nf + 1) * 8, f = rem >> 3, p = rem & 7;
+    for (int i = t; i < S * (nf + 1) * 16; i += kThreads) {
+        const int q = i / ((nf + 1) * 16), rem = i - q * (nf + 1) * 16, f = rem >> 4, p = rem & 15;
         if (f < nf && offs[f] >= 0) continue;
         *reinterpret_cast<float4 *>(sS + q * rowb + f * kSlotBytes + p * 16) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -461,16 +467,29 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             const int64_t o = f < nf ? offs[f] : -1;
             o16[k] = o < 0 ? 0xFFFFFFFFu : uint32_t(o >> 4);
         }
-        int q = 0;                                   // ring buffer of stage st
-        uint32_t ph = 0;                             // its phase: (st / S) & 1
-        for (int st = 0; st < nstage && ok; ++st) {
-            if (st >= S) ok = mbar_wait_abort(&sy->empty[q], ph ^ 1u, abort, spins);
+        // A ring buffer holds two stages (32 grid points): the lane copies
+        // piece p of each stage; the last buffer of an odd stage count holds
+        // one
+        int q = 0;                                   // ring buffer sb % S
+        uint32_t ph = 0;                             // its phase: (sb / S) & 1
+        const int nbuf = (nstage + 1) / 2;
+        for (int sb = 0; sb < nbuf && ok; ++sb) {
+            if (sb >= S) ok = mbar_wait_abort(&sy->empty[q], ph ^ 1u, abort, spins);
             if (!ok) break;
-            const float2 *src = dstore + x0 + int64_t(st) * kTX + 2 * p;
+            const float2 *src = dstore + x0 + int64_t(sb) * (2 * kTX) + 2 * p;
             const uint32_t dst = su32(sS + q * rowb + f0 * kSlotBytes + p * 16);
+            if (2 * sb + 1 < nstage) {
 #pragma unroll
-            for (int k = 0; k < kProdFields; ++k)
-                if (o16[k] != 0xFFFFFFFFu) cp_async16(dst + 8 * k * kSlotBytes, src + (int64_t(o16[k]) << 4));
+                for (int k = 0; k < kProdFields; ++k)
+                    if (o16[k] != 0xFFFFFFFFu) {
+                        cp_async16(dst + 8 * k * kSlotBytes, src + (int64_t(o16[k]) << 4));
+                        cp_async16(dst + 8 * k * kSlotBytes + kTX * 8, src + (int64_t(o16[k]) << 4) + kTX);
+                    }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kProdFields; ++k)
+                    if (o16[k] != 0xFFFFFFFFu) cp_async16(dst + 8 * k * kSlotBytes, src + (int64_t(o16[k]) << 4));
+            }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(su32(&sy->full[q])) : "memory");
             if (++q == S) { q = 0; ph ^= 1u; }
         }
