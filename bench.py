@@ -229,13 +229,16 @@ def fft_crosscheck(plan, field, ws, box):
 
 
 def _peaks():
-    """Measured peaks of this GPU type (written by the harness), or the fallback."""
+    """Measured peaks of this GPU type (written by the harness), or the
+    fallback: bf16 dense TFLOP/s as a burst and sustained over a seconds-long
+    loop, HBM copy GB/s, and which of the two sources."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             d = json.load(fh)
-        return float(d["bf16_tflops"]), float(d["hbm_gbs"]), "measured"
+        burst = float(d["bf16_tflops"])
+        return burst, float(d.get("bf16_tflops_sustained", burst)), float(d["hbm_gbs"]), "measured"
     except (OSError, ValueError, KeyError):
-        return 1900.0, 6800.0, "fallback"
+        return 1900.0, 1700.0, 6800.0, "fallback"
 
 
 def golden_errors(workload_name, field, out, W):
@@ -489,11 +492,15 @@ def run_ours(args):
     # distinct pair product.
     s2_ms = st_ms["step2"] / args.steps
     achieved = flops["step2"] / (s2_ms / 1e3) / 1e12
-    bf16, _, src = _peaks()
+    bf16, bf16_sus, _, src = _peaks()
     if args.precision == "mixed_tc":
-        peak = bf16 * TF32_PER_BF16
+        # Step II runs for most of every step, back to back over the timed
+        # region: the peak sustained over a seconds-long loop applies
+        peak = bf16_sus * TF32_PER_BF16
         roof = {"kernel": "k_step2_tc (Step II triple sums, tcgen05 kind::tf32)", "bound": "tensor",
-                "peak_source": f"tf32 dense: bf16 burst of {src} x {TF32_PER_BF16:.4f} (nominal 1.1 / 2.25 PFLOP/s)"}
+                "peak_source": f"tf32 dense: bf16 sustained (seconds-long loop) of {src} x {TF32_PER_BF16:.4f} "
+                               f"(nominal 1.1 / 2.25 PFLOP/s)",
+                "frac_of_burst_peak": achieved / (bf16 * TF32_PER_BF16)}
     else:
         peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
         roof = {"kernel": "k_step2 (Step II triple sums, FP32 FMA)", "bound": "alu",
@@ -506,7 +513,7 @@ def run_ours(args):
                  "flops_per_estimate": flops["step2"], "ms_per_estimate": s2_ms, "launches_per_estimate": n2})
     # Step I (HBM-bound transforms): algorithmic bytes = the D store written
     # once + the kept planes of Delta read once, over its own event time
-    bf16_, hbm, src_ = _peaks()
+    _, _, hbm, src_ = _peaks()
     s1_ms = st_ms["step1"] / args.steps
     s1_bytes = plan.info["dstore_bytes"] + (ng // 3 + 1) * ng * ng * (16 if args.precision == "fp64" else 8)
     roof1 = {"kernels": "k_ring_gather + k_fft_rows_T (Step I, per reduction grid)", "bound": "hbm",
