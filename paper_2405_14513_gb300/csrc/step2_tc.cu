@@ -149,8 +149,9 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 //   warp 8     issues the 12 MMAs of a stage (one elected lane) into
 //              accumulator buffer st & 1 (tensor-memory columns from 64 NA,
 //              NC apart with three A buffers, 64 apart with two).  The MMAs
-//              of stage st wait for A(st) and for the read of stage st - 2's
-//              accumulators.  (A second issuer with an accumulator of its
+//              of stage st wait for A(st) only: every compute thread read
+//              stage st - 2's accumulators (the buffer they overwrite) before
+//              it signalled A(st).  (A second issuer with an accumulator of its
 //              own was slower: a second accumulator doubles the compute
 //              warps' reads);
 //   warps 9-10 stage the fields of each stage in shared memory (cp.async,
@@ -161,19 +162,18 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 //   empty[q]  ring buffer q has been read             (256 compute arrivals)
 //   aready[a] A and B (high, low) of buffer a written (256 compute arrivals)
 //   mdone[b]  the MMAs into accumulator b are done    (commit)
-//   dfree[b]  accumulator b has been read             (256 compute arrivals)
 //   drain     every MMA the block issued is done      (commit; before the
 //             tensor memory is freed, also when the block gives up early)
 // A barrier's next phase cannot complete before its waiters have seen the
 // current one: A(st + NA) is formed only after the accumulators of stage st
 // were read, which waited for mdone of stage st, and the MMAs of stage
-// st + 2 wait for that read.
+// st + 2 wait for A(st + 2), signalled after that read.
 constexpr int kThreads = 352;
 constexpr int kCompute = 256;
 constexpr int kProdFields = (kTcMaxSlots + kTcMaxCols + 7) / 8;   // fields per producer lane
 
 struct TcSync {
-    uint64_t full[kTcMaxRing], empty[kTcMaxRing], aready[3], mdone[2], dfree[2], drain;
+    uint64_t full[kTcMaxRing], empty[kTcMaxRing], aready[3], mdone[2], drain;
     uint32_t tmem;
     int abort;
 };
@@ -283,8 +283,9 @@ template <int NC> __device__ constexpr uint32_t acc_step() { return tc_abuf(NC) 
 // stage st - (NA - 1).  With two buffers the sums of stage st - 1 are read
 // after forming stage st (the MMAs of st - 1 run meanwhile); with three, the
 // sums of stage st - 2 are read first, so that the MMAs of stage st (which
-// wait for that read) can start as soon as A(st) is written, and have the
-// whole next stage to finish.  Returns false if a wait gave up.  B piece p
+// overwrite that accumulator buffer, and wait only for A(st), signalled
+// after the read) can start as soon as A(st) is written, and have the whole
+// next stage to finish.  Returns false if a wait gave up.  B piece p
 // (grid points 2p, 2p + 1) of column c goes to core matrix (K block p, rows
 // 8 (c / 8) ..), row c % 8; this thread's pieces are i = t and t + 256
 // (i = p NC + c), fixed for the tile, so their offsets are computed once.
@@ -355,8 +356,9 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
         if (!mbar_wait_abort(&sy->mdone[b], uint32_t(s >> 1) & 1, ca.abort, ca.spins)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
         add_accumulator<NH>(ca.tlane + acc_col0<NC>() + acc_step<NC>() * b + NH * ca.half, acc);
+        // ordered before this thread's next signal of A, which the MMAs that
+        // overwrite buffer b wait for
         asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        mbar_arrive(&sy->dfree[b]);
         return true;
     };
     for (int st = 0; st < ca.nstage + LAG; ++st) {
@@ -420,10 +422,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             mbar_init(&sy->empty[q], kCompute);
         }
         for (int b = 0; b < NA; ++b) mbar_init(&sy->aready[b], kCompute);
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sy->mdone[b], 1);
-            mbar_init(&sy->dfree[b], kCompute);
-        }
+        for (int b = 0; b < 2; ++b) mbar_init(&sy->mdone[b], 1);
         mbar_init(&sy->drain, 1);
         sy->abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -506,7 +505,6 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             for (int st = 0; st < nstage && ok; ++st) {
                 const int b = st & 1;                           // accumulator buffer
                 ok = mbar_wait_abort(&sy->aready[ia], pa, abort, spins);
-                if (ok && st >= 2) ok = mbar_wait_abort(&sy->dfree[b], uint32_t((st - 2) >> 1) & 1, abort, spins);
                 ok = __all_sync(0xFFFFFFFFu, ok);
                 if (!ok) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
