@@ -159,7 +159,12 @@ __device__ __forceinline__ void add_accumulator(uint32_t tcol, float (&acc)[NH])
 //              a field row, waited for and released once per two stages).
 // mbarriers (phase k of a barrier = its k-th use):
 //   full[q]   the data of ring buffer q landed        (64 producer arrivals)
-//   empty[q]  ring buffer q has been read             (256 compute arrivals)
+//   empty[q]  ring buffer q has been read             (1 arrival: the MMA warp,
+//                                                      once it has seen A of
+//                                                      the buffer's last stage,
+//                                                      which every compute
+//                                                      thread signals after its
+//                                                      reads of the buffer)
 //   aready[a] A and B (high, low) of buffer a written (256 compute arrivals)
 //   mdone[b]  the MMAs into accumulator b are done    (commit)
 //   drain     every MMA the block issued is done      (commit; before the
@@ -316,8 +321,8 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
     int ia = 0;                                  // A / B buffer of stage st: st % NA
     // A and B of stage st (half st & 1 of ring buffer q) into buffer ia
     // (last read by the MMAs of stage st - NA, complete: their sums have
-    // been read); the ring buffer is waited for at its first stage and
-    // released after its second (or the last stage)
+    // been read); the ring buffer is waited for at its first stage and left
+    // after its second (or the last stage); the MMA warp releases it
     auto form = [&](int st) -> bool {
         const int h = (st & 1) * (kTX * 8);
         if (h == 0 && !mbar_wait_abort(&sy->full[q], ph, ca.abort, ca.spins)) return false;
@@ -334,7 +339,6 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
             *reinterpret_cast<uint4 *>(ca.sLo + o) = l;
         }
         if (h != 0 || st + 1 == ca.nstage) {
-            mbar_arrive(&sy->empty[q]);
             if (++q == ca.S) {
                 q = 0;
                 ph ^= 1u;
@@ -419,7 +423,7 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
     if (t == 0) {
         for (int q = 0; q < S; ++q) {
             mbar_init(&sy->full[q], 64);
-            mbar_init(&sy->empty[q], kCompute);
+            mbar_init(&sy->empty[q], 1);
         }
         for (int b = 0; b < NA; ++b) mbar_init(&sy->aready[b], kCompute);
         for (int b = 0; b < 2; ++b) mbar_init(&sy->mdone[b], 1);
@@ -502,11 +506,19 @@ k_step2_tc(TcArgs args, int64_t unit0, const float2 *__restrict__ dstore)
             const uint64_t dh = smem_desc(su32(sHi), LBO, SBO), dl = smem_desc(su32(sLo), LBO, SBO);
             int ia = 0;                                         // A / B buffer of stage st
             uint32_t pa = 0;                                    // its phase: (st / NA) & 1
+            int qr = 0;                                         // ring buffer of stage st
             for (int st = 0; st < nstage && ok; ++st) {
                 const int b = st & 1;                           // accumulator buffer
                 ok = mbar_wait_abort(&sy->aready[ia], pa, abort, spins);
                 ok = __all_sync(0xFFFFFFFFu, ok);
                 if (!ok) break;
+                // A(st) signalled by every compute thread: at the last stage
+                // of a ring buffer, all its reads are done (the MMAs do not
+                // read the ring)
+                if ((st & 1) || st + 1 == nstage) {
+                    if (lane == 0) mbar_arrive(&sy->empty[qr]);
+                    if (++qr == S) qr = 0;
+                }
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t a = tmem + 64 * ia;
                 const uint32_t d = tmem + acc_col0<NC>() + acc_step<NC>() * b;
