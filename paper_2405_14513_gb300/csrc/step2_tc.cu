@@ -359,10 +359,9 @@ __device__ __forceinline__ bool compute_loop(const CompArgs &ca, float (&acc)[NC
         const int b = s & 1;
         if (!mbar_wait_abort(&sy->mdone[b], uint32_t(s >> 1) & 1, ca.abort, ca.spins)) return false;
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // (ordered before this thread's next signal of A, which the MMAs that
+        // overwrite buffer b wait for, by the fence that precedes it)
         add_accumulator<NH>(ca.tlane + acc_col0<NC>() + acc_step<NC>() * b + NH * ca.half, acc);
-        // ordered before this thread's next signal of A, which the MMAs that
-        // overwrite buffer b wait for
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
         return true;
     };
     for (int st = 0; st < ca.nstage + LAG; ++st) {
