@@ -169,7 +169,7 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 STEP2_SOURCE = {
     "mixed_tc": [("step2_tc.cu", None, "template <int NC>\ncudaError_t launch_class"),
                  ("plan.hpp", "constexpr int kTcRows", "struct TcUnit"),
-                 ("plan.cpp", "std::string build_tc(", "}  // namespace\n\nstd::string enumerate(")],
+                 ("plan.cpp", "std::string build_tc(", "void build_views(")],
     "mixed": [("kernels.cu", None, None)], "fp32": [("kernels.cu", None, None)],
     "fp64": [("kernels.cu", None, None)],
 }

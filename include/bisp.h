@@ -93,14 +93,15 @@ typedef struct {
     int64_t n_combos;                /* accepted combinations, one of each +-n pair   */
     int64_t n_pairs;                 /* plane pairs (n1, n2) with a combination       */
     int64_t n_items;                 /* Step-II blocks (pair, grid, x chunk, tiles)   */
-    double triple_products;          /* sum over combinations of grid points summed   */
+    double triple_products;          /* sum over combinations of the points of its    */
+                                     /* smallest exact reduction grid                 */
     size_t dstore_bytes;             /* D-field store of one field                    */
     size_t workspace_bytes;          /* estimator_workspace_bytes(plan, 1)            */
     size_t resident_bytes;           /* device memory owned by the plan               */
     int n_views;                     /* binnings (bisp_view_info), >= 1                */
     int64_t out_doubles;             /* doubles of B per field (all views)            */
     /* Step-II work on the tensor cores (MIXED_TC; 0 otherwise), in grid points: */
-    double pair_products;            /* distinct pair products D1 D2 the sums need     */
+    double pair_products;            /* distinct pair products D1 D2 on those grids   */
     double tc_row_points;            /* pair products the tiles form (rows x points)   */
     double tc_lane_points;           /* tensor-memory lanes x points of all tiles      */
     double tc_mma_products;          /* lanes x window columns x points (MMA work)     */

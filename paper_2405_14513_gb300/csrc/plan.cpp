@@ -444,6 +444,44 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
         for (auto &t : th) t.join();
     }
 
+    // Work of the sums on each combination's smallest exact grid (the
+    // algorithmic figures the plan reports): the grid points of every
+    // combination, and of every distinct (pair, r1, r2, grid) product D1 D2.
+    // acc is ordered by (r1, r2, r3), so the grids of one (r1, r2) are
+    // collected in one run.
+    P.triple_products = 0;
+    P.pair_products = 0;
+    for (const PairOut &po : outs)
+        for (size_t i = 0; i < po.acc.size();) {
+            uint32_t levs = 0;
+            size_t j = i;
+            for (; j < po.acc.size() && po.acc[j].r1 == po.acc[i].r1 && po.acc[j].r2 == po.acc[i].r2; ++j) {
+                const double m = double(R.grid[po.acc[j].lev]);
+                P.triple_products += m * m;
+                levs |= 1u << po.acc[j].lev;
+            }
+            for (int lv = 0; lv < R.ngrid; ++lv)
+                if (levs >> lv & 1u) P.pair_products += double(R.grid[lv]) * double(R.grid[lv]);
+            i = j;
+        }
+    // tcgen05: the combinations of one (r1, r2) of a pair are summed on one
+    // grid, the largest their r3 need.  On any grid above the bound the sum
+    // is exact (see triple_level), and a row's pair product D1 D2 is then
+    // formed once instead of once per grid; forming it, not the MMAs that
+    // apply it to the r3 window, is what the tensor-core tiles spend their
+    // time on.  The CUDA-core tiles do work per combination and keep the
+    // smallest grid.
+    if (P.tensor)
+        for (PairOut &po : outs)
+            for (size_t i = 0; i < po.acc.size();) {
+                size_t j = i;
+                uint8_t top = 0;
+                for (; j < po.acc.size() && po.acc[j].r1 == po.acc[i].r1 && po.acc[j].r2 == po.acc[i].r2; ++j)
+                    top = std::max(top, po.acc[j].lev);
+                for (size_t q = i; q < j; ++q) po.acc[q].lev = top;
+                i = j;
+            }
+
     // used[l][n][r]: D fields to store
     std::vector<uint8_t> used(size_t(kMaxLevels) * (nz + 1) * kMaxRings, 0);
     auto U_ = [&](int lv, int n, int r) -> uint8_t & {
@@ -458,8 +496,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
     P.ntri_s.clear();
     P.n_combos = 0;
     P.n_pairs = 0;
-    P.triple_products = 0;
-    P.pair_products = 0;
     P.max_slots = 0;
     std::vector<Unit> unit_tmpl;                 // per group: tile ranges and staged rings
     std::vector<int32_t> group_unit0(1, 0);      // first template of each group
@@ -478,8 +514,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             G.c0 = cidx;
             G.self_conj = (n1 == 0 && n2 == 0) ? 1 : 0;
             int ncombo = 0;
-            int64_t nrowpair = 0;
-            int last_r1 = -1, last_r2 = -1;
             size_t i = 0;
             while (i < po.acc.size()) {
                 if (po.acc[i].lev != lv) { ++i; continue; }
@@ -493,11 +527,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
                     ++r3;
                 }
                 P.rows.push_back(Row{a.r1, a.r2, a.r3, uint8_t(j - i), ncombo});
-                if (a.r1 != last_r1 || a.r2 != last_r2) {
-                    ++nrowpair;
-                    last_r1 = a.r1;
-                    last_r2 = a.r2;
-                }
                 for (size_t q = i; q < j; ++q) {
                     const Acc &c = po.acc[q];
                     Record rec;
@@ -516,8 +545,6 @@ std::string enumerate(HostPlan &P, int64_t x_chunk)
             G.ncombo = ncombo;
             const int64_t M2 = int64_t(G.M) * G.M;
             G.nchunk = int32_t((M2 + x_chunk - 1) / x_chunk);
-            P.triple_products += double(ncombo) * double(M2);
-            P.pair_products += double(nrowpair) * double(M2);
             cidx += ncombo;
 
             if (P.tensor) {             // tcgen05 tiles span groups: built after the loop

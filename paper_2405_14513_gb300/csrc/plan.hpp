@@ -220,8 +220,8 @@ struct HostPlan {
     int64_t n_combos = 0;
     int64_t n_partials = 0;
     int64_t n_pairs = 0;
-    double triple_products = 0;          // sum over combinations of M^2
-    double pair_products = 0;            // sum over distinct (group, r1, r2) of M^2
+    double triple_products = 0;          // sum over combinations of M^2 (M: its smallest exact grid)
+    double pair_products = 0;            // sum over distinct (pair, r1, r2, smallest grid) of M^2
     std::vector<int32_t> combo_bin;      // S order
     std::vector<Record> records_s;      // S order (moved to bin order later)
     std::vector<double> ntri_s;         // N_tri per combination, S order
