@@ -14,9 +14,9 @@
 //   k_ntri          N_tri = M^-2 sum_y I1 I2 I3 on the unit fields (Eq. Ntri2)
 //
 // All transforms use exp(-i k.x), the sign of Eq. iFT.  Transform lengths
-// are 2^q or 3 x 2^q (the reduction grids of the plan); the twiddle tables,
-// computed on the host in double, are tw2[k] = exp(-2 pi i k / 2^lg2) and
-// tw3[k] = exp(-2 pi i k / (3 x 2^lg3)).
+// are 2^q, 3 x 2^q or 5 x 2^q (N_g and the reduction grids of the plan); the
+// twiddle tables, computed on the host in double, are
+// twF[k] = exp(-2 pi i k / (F x 2^lgF)), F = 1 (tw2), 3, 5.
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -75,22 +75,21 @@ struct DivIter {
     }
 };
 
-// Stockham transform of nrows rows of length M = 2^q or 3 x 2^q held in
-// shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M): one
-// radix-3 stage first when 3 divides M, then radix-8 stages and, for what
-// is left of the power of two, one radix-4 or radix-2 stage.  Every thread
-// of the block takes part; the caller synchronises before the call.  The
-// result is in the returned buffer (a or b).
-template <typename C>
-__device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
+// Stockham transform of nrows rows of length M = F x 2^q (F = 1, 3 or 5)
+// held in shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M):
+// one radix-F stage first when F > 1, then radix-8 stages and, for what is
+// left of the power of two, one radix-4 or radix-2 stage.  Every thread of
+// the block takes part; the caller synchronises before the call.  The result
+// is in the returned buffer (a or b).  Every index split below is a shift, or
+// a shift and a division by the constant F.
+template <typename C, int F>
+__device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
 {
     using Rr = decltype(a[0].x);
-    // M = 2^p or 3 x 2^p: every index split below is a shift, or a shift and
-    // a division by the constant 3
-    const int p = __ffs(M) - 1;
-    const bool has3 = (M >> p) == 3;
+    const int p = __ffs(M) - 1;                 // M = F 2^p
+    auto divF = [](int x) { return F == 1 ? x : int(unsigned(x) / unsigned(F)); };
     int Ns = 1;
-    if (has3) {
+    if (F == 3) {
         const int third = M / 3;
         const int total = nrows * third;
         const Rr h = Rr(0.86602540378443864676);   // sqrt(3)/2
@@ -112,10 +111,44 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
         a = b;
         b = t2;
         Ns = 3;
+    } else if (F == 5) {
+        // 5-point DFT of v_k = x[j + k M/5], w = exp(-2 pi i/5):
+        //   y_0 = v0 + s1 + s2,  s1 = v1 + v4,  s2 = v2 + v3,  d1 = v1 - v4,  d2 = v2 - v3,
+        //   y_1, y_4 = v0 + c1 s1 + c2 s2 -/+ i (n1 d1 + n2 d2),
+        //   y_2, y_3 = v0 + c2 s1 + c1 s2 -/+ i (n2 d1 - n1 d2),
+        // c_m = cos(2 pi m/5), n_m = sin(2 pi m/5)
+        const int fifth = M / 5;
+        const int total = nrows * fifth;
+        const Rr c1 = Rr(0.30901699437494742410), c2 = Rr(-0.80901699437494742410);
+        const Rr n1 = Rr(0.95105651629515357212), n2 = Rr(0.58778525229247312917);
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int row = t >> p, j = t & (fifth - 1);
+            const C *src = a + row * P + j;
+            const C v0 = src[0], v1 = src[fifth], v2 = src[2 * fifth], v3 = src[3 * fifth], v4 = src[4 * fifth];
+            const C s1 = cadd(v1, v4), s2 = cadd(v2, v3), d1 = csub(v1, v4), d2 = csub(v2, v3);
+            C a1, a2, b1, b2;
+            a1.x = v0.x + c1 * s1.x + c2 * s2.x; a1.y = v0.y + c1 * s1.y + c2 * s2.y;
+            a2.x = v0.x + c2 * s1.x + c1 * s2.x; a2.y = v0.y + c2 * s1.y + c1 * s2.y;
+            b1.x = n1 * d1.x + n2 * d2.x; b1.y = n1 * d1.y + n2 * d2.y;
+            b2.x = n2 * d1.x - n1 * d2.x; b2.y = n2 * d1.y - n1 * d2.y;
+            // -i b = (b.y, -b.x)
+            C *dst = b + row * P + 5 * j;
+            C y;
+            y.x = v0.x + s1.x + s2.x; y.y = v0.y + s1.y + s2.y; dst[0] = y;
+            y.x = a1.x + b1.y; y.y = a1.y - b1.x; dst[1] = y;
+            y.x = a2.x + b2.y; y.y = a2.y - b2.x; dst[2] = y;
+            y.x = a2.x - b2.y; y.y = a2.y + b2.x; dst[3] = y;
+            y.x = a1.x - b1.y; y.y = a1.y + b1.x; dst[4] = y;
+        }
+        __syncthreads();
+        C *t2 = a;
+        a = b;
+        b = t2;
+        Ns = 5;
     }
-    const C *wt = has3 ? tw.tw3 : tw.tw2;
-    const int lg = has3 ? tw.lg3 : tw.lg2;
-    int s = 0;                                  // Ns = 2^s (times 3 if has3)
+    const C *wt = F == 5 ? tw.tw5 : (F == 3 ? tw.tw3 : tw.tw2);
+    const int lg = F == 5 ? tw.lg5 : (F == 3 ? tw.lg3 : tw.lg2);
+    int s = 0;                                  // Ns = F 2^s
     while (Ns < M) {
         if (M / Ns >= 8) {
             // radix 8: v_r = x[j + r M/8] w^(rk), w = exp(-2 pi i / (8 Ns)),
@@ -127,9 +160,9 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
             const int sh = lg - s - 3;
             const Rr r2 = Rr(0.70710678118654752440);   // 1/sqrt(2)
             for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int row = has3 ? int(unsigned(t >> (p - 3)) / 3u) : (t >> (p - 3));
+                const int row = divF(t >> (p - 3));
                 const int j = t - row * eighth;
-                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int q = divF(j >> s);
                 const int k = j - q * Ns;
                 const C *src = a + row * P + j;
                 C v[8];
@@ -174,9 +207,9 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
             const int total = nrows * quarter;
             const int sh = lg - s - 2;
             for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int row = has3 ? int(unsigned(t >> (p - 2)) / 3u) : (t >> (p - 2));
+                const int row = divF(t >> (p - 2));
                 const int j = t - row * quarter;
-                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int q = divF(j >> s);
                 const int k = j - q * Ns;
                 const C *src = a + row * P + j;
                 const C v0 = src[0];
@@ -201,9 +234,9 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
             const int total = nrows * half;
             const int sh = lg - s - 1;
             for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                const int row = has3 ? int(unsigned(t >> (p - 1)) / 3u) : (t >> (p - 1));
+                const int row = divF(t >> (p - 1));
                 const int j = t - row * half;
-                const int q = has3 ? int(unsigned(j >> s) / 3u) : (j >> s);
+                const int q = divF(j >> s);
                 const int k = j - q * Ns;
                 C v0 = a[row * P + j];
                 C v1 = cmul(a[row * P + j + half], __ldg(&wt[k << sh]));
@@ -220,6 +253,16 @@ __device__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &t
         b = t2;
     }
     return a;
+}
+
+// Transform of rows of length M = 2^q, 3 x 2^q or 5 x 2^q (block-uniform dispatch)
+template <typename C>
+__device__ __forceinline__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
+{
+    const int odd = M >> (__ffs(M) - 1);
+    if (odd == 5) return fft_smem_f<C, 5>(a, b, M, P, nrows, tw);
+    if (odd == 3) return fft_smem_f<C, 3>(a, b, M, P, nrows, tw);
+    return fft_smem_f<C, 1>(a, b, M, P, nrows, tw);
 }
 
 // ---------------------------------------------------------------------------

@@ -82,10 +82,14 @@ def test_forward_transform_planes(c64):
 
 
 def test_step1_dfields_on_every_grid(c64):
+    """Stored D fields of sampled combinations of every reduction grid in use
+    (2^q, 3 x 2^q and 5 x 2^q sides) against the oracle's direct evaluation."""
     tab = c64.plan.combo_table()
     rng = np.random.default_rng(3)
     seen = set()
-    for k in rng.choice(len(tab["ints"]), size=60, replace=False):
+    pick = np.concatenate([rng.choice(np.flatnonzero(tab["grid"] == M), size=min(6, int((tab["grid"] == M).sum())),
+                                      replace=False) for M in np.unique(tab["grid"])])
+    for k in pick:
         n1, n2, n3, r1, r2, r3 = tab["ints"][k]
         M = int(tab["grid"][k])
         for n, r in ((n1, r1), (n2, r2), (n3, r3)):
@@ -97,7 +101,8 @@ def test_step1_dfields_on_every_grid(c64):
             want = O.dfield_at(c64.field64, c64.L, int(r), abs(int(n)), M)
             assert np.abs(got - want).max() < 2e-6 * max(np.abs(want).max(), 1e-30), key
     grids = {int(M) for M, _, _ in seen}
-    assert any(M % 3 == 0 for M in grids) and any(M % 3 for M in grids), grids
+    assert any(M % 3 == 0 for M in grids) and any(M % 5 == 0 for M in grids), grids
+    assert any(M % 3 and M % 5 for M in grids), grids
 
 
 def test_combination_table_matches_oracle(c64):
