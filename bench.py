@@ -169,6 +169,7 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 STEP2_SOURCE = {
     "mixed_tc": [("step2_tc.cu", None, "template <int NC>\ncudaError_t launch_class"),
                  ("plan.hpp", "constexpr int kTcRows", "struct TcUnit"),
+                 ("plan.cpp", "bool build_rings(", "int half_unit_bin("),
                  ("plan.cpp", "std::string build_tc(", "void build_views(")],
     "mixed": [("kernels.cu", None, None)], "fp32": [("kernels.cu", None, None)],
     "fp64": [("kernels.cu", None, None)],

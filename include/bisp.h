@@ -390,8 +390,8 @@ int estimator_combo_sums(const bisp_plan *plan, const void *workspace, double *S
 /* After estimator_estimate on this workspace: D(r, n, x) of Eq. iFT of the
  * last field at the M x M points x = (N_g/M) y, y integer, i.e.
  * sum_{u in r} Delta(u, n) exp(-2 pi i u.y / M), as stored for the Step-II
- * reduction.  M is one of the plan's reduction grid sides (2^q, 3 x 2^q or
- * 5 x 2^q, a multiple of 4, 8 <= M <= N_g).  out: HOST pointer [M][M][2]
+ * reduction.  M is one of the plan's reduction grid sides (F x 2^q, F = 1,
+ * 3, 5 or 7, a multiple of 4, 8 <= M <= N_g).  out: HOST pointer [M][M][2]
  * (y_x slow, y_y fast), in double.  Returns BISP_INVALID_ARG when (M, n, r) is not stored. */
 int estimator_dfield(const bisp_plan *plan, const void *workspace, int M, int n, int r,
                      double *out, void *stream);

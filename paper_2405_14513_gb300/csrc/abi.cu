@@ -511,15 +511,17 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
     for (int l = 0; l < R.ngrid; ++l) p->grid_arg.M[l] = R.grid[l];
     // twiddles in double: exp(-2 pi i k / (F x 2^lgF)), k < 7/8 of F x 2^lgF
     // (radix-8 stages reach seven eighths of the circle), for the lengths
-    // F x 2^q <= N_g of the transforms, F = 1, 3, 5
+    // F x 2^q <= N_g of the transforms, F = 1, 3, 5, 7
     {
         const int ng = desc->n_g;
-        int lg2 = 0, lg3 = 0, lg5 = 0;
+        int lg2 = 0, lg3 = 0, lg5 = 0, lg7 = 0;
         while ((2 << lg2) <= ng) ++lg2;
         while (3 * (2 << lg3) <= ng) ++lg3;
         while (5 * (2 << lg5) <= ng) ++lg5;
+        while (7 * (2 << lg7) <= ng) ++lg7;
         if (lg3 < 1) lg3 = 1;
         if (lg5 < 2) lg5 = 2;
+        if (lg7 < 2) lg7 = 2;
         auto table = [&](int base, int count, float2 **df, double2 **dd) -> int {
             std::vector<double2> twd(count);
             std::vector<float2> twf(count);
@@ -531,14 +533,15 @@ int build_plan(bisp_plan *p, const bisp_desc *desc, cudaStream_t s)
             int st = upload(p, dd, twd, s);
             return st ? st : upload(p, df, twf, s);
         };
-        float2 *f2 = nullptr, *f3 = nullptr, *f5 = nullptr;
-        double2 *d2 = nullptr, *d3 = nullptr, *d5 = nullptr;
+        float2 *f2 = nullptr, *f3 = nullptr, *f5 = nullptr, *f7 = nullptr;
+        double2 *d2 = nullptr, *d3 = nullptr, *d5 = nullptr, *d7 = nullptr;
         int st = table(1 << lg2, (7 * (1 << lg2) + 7) / 8, &f2, &d2);
         if (!st) st = table(3 << lg3, (7 * (3 << lg3) + 7) / 8, &f3, &d3);
         if (!st) st = table(5 << lg5, (7 * (5 << lg5) + 7) / 8, &f5, &d5);
+        if (!st) st = table(7 << lg7, (7 * (7 << lg7) + 7) / 8, &f7, &d7);
         if (st) return st;
-        p->tw_f = Twiddles<float2>{f2, f3, lg2, lg3, f5, lg5};
-        p->tw_d = Twiddles<double2>{d2, d3, lg2, lg3, d5, lg5};
+        p->tw_f = Twiddles<float2>{f2, f3, lg2, lg3, f5, lg5, f7, lg7};
+        p->tw_d = Twiddles<double2>{d2, d3, lg2, lg3, d5, lg5, d7, lg7};
     }
     // Y_lm normalisations
     {

@@ -14,9 +14,9 @@
 //   k_ntri          N_tri = M^-2 sum_y I1 I2 I3 on the unit fields (Eq. Ntri2)
 //
 // All transforms use exp(-i k.x), the sign of Eq. iFT.  Transform lengths
-// are 2^q, 3 x 2^q or 5 x 2^q (N_g and the reduction grids of the plan); the
-// twiddle tables, computed on the host in double, are
-// twF[k] = exp(-2 pi i k / (F x 2^lgF)), F = 1 (tw2), 3, 5.
+// are 2^q, 3 x 2^q, 5 x 2^q or 7 x 2^q (N_g and the reduction grids of the
+// plan); the twiddle tables, computed on the host in double, are
+// twF[k] = exp(-2 pi i k / (F x 2^lgF)), F = 1 (tw2), 3, 5, 7.
 #include "kernels.cuh"
 
 #include <algorithm>
@@ -75,7 +75,7 @@ struct DivIter {
     }
 };
 
-// Stockham transform of nrows rows of length M = F x 2^q (F = 1, 3 or 5)
+// Stockham transform of nrows rows of length M = F x 2^q (F = 1, 3, 5 or 7)
 // held in shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M):
 // one radix-F stage first when F > 1, then radix-8 stages and, for what is
 // left of the power of two, one radix-4 or radix-2 stage.  Every thread of
@@ -123,8 +123,9 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
         const Rr n1 = Rr(0.95105651629515357212), n2 = Rr(0.58778525229247312917);
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             const int row = t >> p, j = t & (fifth - 1);
-            const C *src = a + row * P + j;
-            const C v0 = src[0], v1 = src[fifth], v2 = src[2 * fifth], v3 = src[3 * fifth], v4 = src[4 * fifth];
+            const C *src = a + row * P;
+            const C v0 = src[j], v1 = src[j + fifth], v2 = src[j + 2 * fifth], v3 = src[j + 3 * fifth],
+                    v4 = src[j + 4 * fifth];
             const C s1 = cadd(v1, v4), s2 = cadd(v2, v3), d1 = csub(v1, v4), d2 = csub(v2, v3);
             C a1, a2, b1, b2;
             a1.x = v0.x + c1 * s1.x + c2 * s2.x; a1.y = v0.y + c1 * s1.y + c2 * s2.y;
@@ -132,22 +133,60 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
             b1.x = n1 * d1.x + n2 * d2.x; b1.y = n1 * d1.y + n2 * d2.y;
             b2.x = n2 * d1.x - n1 * d2.x; b2.y = n2 * d1.y - n1 * d2.y;
             // -i b = (b.y, -b.x)
-            C *dst = b + row * P + 5 * j;
+            C *dst = b + row * P;
             C y;
-            y.x = v0.x + s1.x + s2.x; y.y = v0.y + s1.y + s2.y; dst[0] = y;
-            y.x = a1.x + b1.y; y.y = a1.y - b1.x; dst[1] = y;
-            y.x = a2.x + b2.y; y.y = a2.y - b2.x; dst[2] = y;
-            y.x = a2.x - b2.y; y.y = a2.y + b2.x; dst[3] = y;
-            y.x = a1.x - b1.y; y.y = a1.y + b1.x; dst[4] = y;
+            y.x = v0.x + s1.x + s2.x; y.y = v0.y + s1.y + s2.y; dst[5 * j] = y;
+            y.x = a1.x + b1.y; y.y = a1.y - b1.x; dst[5 * j + 1] = y;
+            y.x = a2.x + b2.y; y.y = a2.y - b2.x; dst[5 * j + 2] = y;
+            y.x = a2.x - b2.y; y.y = a2.y + b2.x; dst[5 * j + 3] = y;
+            y.x = a1.x - b1.y; y.y = a1.y + b1.x; dst[5 * j + 4] = y;
         }
         __syncthreads();
         C *t2 = a;
         a = b;
         b = t2;
         Ns = 5;
+    } else if (F == 7) {
+        // 7-point DFT of v_k = x[j + k M/7], by the same pairing:
+        //   s_k = v_k + v_{7-k},  d_k = v_k - v_{7-k}  (k = 1, 2, 3),
+        //   y_m, y_{7-m} = v0 + sum_k cos(2 pi mk/7) s_k -/+ i sum_k sin(2 pi mk/7) d_k  (m = 1, 2, 3)
+        const int sev = M / 7;
+        const int total = nrows * sev;
+        const Rr c1 = Rr(0.62348980185873353053), c2 = Rr(-0.22252093395631440429), c3 = Rr(-0.90096886790241912624);
+        const Rr n1 = Rr(0.78183148246802980871), n2 = Rr(0.97492791218182360702), n3 = Rr(0.43388373911755812048);
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const int row = t >> p, j = t & (sev - 1);
+            const C *src = a + row * P;
+            C v[7];
+#pragma unroll
+            for (int k = 0; k < 7; ++k) v[k] = src[j + k * sev];
+            const C s1 = cadd(v[1], v[6]), s2 = cadd(v[2], v[5]), s3 = cadd(v[3], v[4]);
+            const C d1 = csub(v[1], v[6]), d2 = csub(v[2], v[5]), d3 = csub(v[3], v[4]);
+            C am[3], bm[3];
+            am[0].x = v[0].x + c1 * s1.x + c2 * s2.x + c3 * s3.x; am[0].y = v[0].y + c1 * s1.y + c2 * s2.y + c3 * s3.y;
+            am[1].x = v[0].x + c2 * s1.x + c3 * s2.x + c1 * s3.x; am[1].y = v[0].y + c2 * s1.y + c3 * s2.y + c1 * s3.y;
+            am[2].x = v[0].x + c3 * s1.x + c1 * s2.x + c2 * s3.x; am[2].y = v[0].y + c3 * s1.y + c1 * s2.y + c2 * s3.y;
+            bm[0].x = n1 * d1.x + n2 * d2.x + n3 * d3.x; bm[0].y = n1 * d1.y + n2 * d2.y + n3 * d3.y;
+            bm[1].x = n2 * d1.x - n3 * d2.x - n1 * d3.x; bm[1].y = n2 * d1.y - n3 * d2.y - n1 * d3.y;
+            bm[2].x = n3 * d1.x - n1 * d2.x + n2 * d3.x; bm[2].y = n3 * d1.y - n1 * d2.y + n2 * d3.y;
+            C *dst = b + row * P;
+            C y;
+            y.x = v[0].x + s1.x + s2.x + s3.x; y.y = v[0].y + s1.y + s2.y + s3.y; dst[7 * j] = y;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                // -i b = (b.y, -b.x)
+                y.x = am[m].x + bm[m].y; y.y = am[m].y - bm[m].x; dst[7 * j + m + 1] = y;
+                y.x = am[m].x - bm[m].y; y.y = am[m].y + bm[m].x; dst[7 * j + 6 - m] = y;
+            }
+        }
+        __syncthreads();
+        C *t2 = a;
+        a = b;
+        b = t2;
+        Ns = 7;
     }
-    const C *wt = F == 5 ? tw.tw5 : (F == 3 ? tw.tw3 : tw.tw2);
-    const int lg = F == 5 ? tw.lg5 : (F == 3 ? tw.lg3 : tw.lg2);
+    const C *wt = F == 7 ? tw.tw7 : (F == 5 ? tw.tw5 : (F == 3 ? tw.tw3 : tw.tw2));
+    const int lg = F == 7 ? tw.lg7 : (F == 5 ? tw.lg5 : (F == 3 ? tw.lg3 : tw.lg2));
     int s = 0;                                  // Ns = F 2^s
     while (Ns < M) {
         if (M / Ns >= 8) {
@@ -164,11 +203,11 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                 const int j = t - row * eighth;
                 const int q = divF(j >> s);
                 const int k = j - q * Ns;
-                const C *src = a + row * P + j;
+                const C *src = a + row * P;
                 C v[8];
-                v[0] = src[0];
+                v[0] = src[j];
 #pragma unroll
-                for (int r = 1; r < 8; ++r) v[r] = cmul(src[r * eighth], __ldg(&wt[(r * k) << sh]));
+                for (int r = 1; r < 8; ++r) v[r] = cmul(src[j + r * eighth], __ldg(&wt[(r * k) << sh]));
                 C e[4], o[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -183,7 +222,8 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                     o[2].x = o[2].y; o[2].y = -x2;
                     o[3].x = (t3.y - t3.x) * r2; o[3].y = -(t3.x + t3.y) * r2;
                 }
-                C *dst = b + row * P + q * 8 * Ns + k;
+                C *dst = b + row * P;
+                const int d0 = q * 8 * Ns + k;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const C *x = h ? o : e;
@@ -192,10 +232,10 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                     C m1 = d02, m3 = d02;                 // d02 -/+ i d13
                     m1.x += d13.y; m1.y -= d13.x;
                     m3.x -= d13.y; m3.y += d13.x;
-                    dst[(0 + h) * Ns] = cadd(s02, s13);
-                    dst[(2 + h) * Ns] = m1;
-                    dst[(4 + h) * Ns] = csub(s02, s13);
-                    dst[(6 + h) * Ns] = m3;
+                    dst[d0 + (0 + h) * Ns] = cadd(s02, s13);
+                    dst[d0 + (2 + h) * Ns] = m1;
+                    dst[d0 + (4 + h) * Ns] = csub(s02, s13);
+                    dst[d0 + (6 + h) * Ns] = m3;
                 }
             }
             Ns *= 8;
@@ -211,21 +251,22 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                 const int j = t - row * quarter;
                 const int q = divF(j >> s);
                 const int k = j - q * Ns;
-                const C *src = a + row * P + j;
-                const C v0 = src[0];
-                const C v1 = cmul(src[quarter], __ldg(&wt[k << sh]));
-                const C v2 = cmul(src[2 * quarter], __ldg(&wt[(2 * k) << sh]));
-                const C v3 = cmul(src[3 * quarter], __ldg(&wt[(3 * k) << sh]));
+                const C *src = a + row * P;
+                const C v0 = src[j];
+                const C v1 = cmul(src[j + quarter], __ldg(&wt[k << sh]));
+                const C v2 = cmul(src[j + 2 * quarter], __ldg(&wt[(2 * k) << sh]));
+                const C v3 = cmul(src[j + 3 * quarter], __ldg(&wt[(3 * k) << sh]));
                 const C s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
-                C *dst = b + row * P + q * 4 * Ns + k;
-                dst[0] = cadd(s02, s13);
-                dst[2 * Ns] = csub(s02, s13);
+                C *dst = b + row * P;
+                const int d0 = q * 4 * Ns + k;
+                dst[d0] = cadd(s02, s13);
+                dst[d0 + 2 * Ns] = csub(s02, s13);
                 // -i d13 = (d13.y, -d13.x)
                 C m1 = d02, m3 = d02;
                 m1.x += d13.y; m1.y -= d13.x;
                 m3.x -= d13.y; m3.y += d13.x;
-                dst[Ns] = m1;
-                dst[3 * Ns] = m3;
+                dst[d0 + Ns] = m1;
+                dst[d0 + 3 * Ns] = m3;
             }
             Ns *= 4;
             s += 2;
@@ -255,11 +296,13 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
     return a;
 }
 
-// Transform of rows of length M = 2^q, 3 x 2^q or 5 x 2^q (block-uniform dispatch)
+// Transform of rows of length M = 2^q, 3 x 2^q, 5 x 2^q or 7 x 2^q
+// (block-uniform dispatch)
 template <typename C>
 __device__ __forceinline__ C *fft_smem(C *a, C *b, int M, int P, int nrows, const Twiddles<C> &tw)
 {
     const int odd = M >> (__ffs(M) - 1);
+    if (odd == 7) return fft_smem_f<C, 7>(a, b, M, P, nrows, tw);
     if (odd == 5) return fft_smem_f<C, 5>(a, b, M, P, nrows, tw);
     if (odd == 3) return fft_smem_f<C, 3>(a, b, M, P, nrows, tw);
     return fft_smem_f<C, 1>(a, b, M, P, nrows, tw);

@@ -23,14 +23,16 @@ struct RingArg {
 
 // Twiddle tables of the transforms: tw2[k] = exp(-2 pi i k / 2^lg2) for
 // lengths 2^q <= 2^lg2, tw3[k] = exp(-2 pi i k / (3 x 2^lg3)) for lengths
-// 3 x 2^q <= 3 x 2^lg3 and tw5[k] = exp(-2 pi i k / (5 x 2^lg5)) for lengths
-// 5 x 2^q <= 5 x 2^lg5 (tw3, tw5 may be null when no such length is used).
+// 3 x 2^q <= 3 x 2^lg3, and likewise tw5 and tw7 for lengths 5 x 2^q and
+// 7 x 2^q (tw3, tw5, tw7 may be null when no such length is used).
 template <typename C> struct Twiddles {
     const C *tw2;
     const C *tw3;
     int lg2, lg3;
     const C *tw5;
     int lg5;
+    const C *tw7;
+    int lg7;
 };
 
 // Side lengths of the plan's reduction grids, by level index.

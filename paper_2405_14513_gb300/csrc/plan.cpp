@@ -52,12 +52,12 @@ bool build_rings(int ng, Rings &R)
         }
     for (int q = 0; q < R.nr; ++q)
         R.kperp[q] = R.count[q] > 0 ? sum[q] / double(R.count[q]) : 0.5 * double(R.e3[q] + R.e3[q + 1]) / 3.0;
-    // reduction grids: 2^k, 3 x 2^k and 5 x 2^k from 8 to N_g, multiples of
-    // 4 (a grid's M^2 points are a whole number of 16-point stages),
-    // ascending
+    // reduction grids: 2^k, 3 x 2^k, 5 x 2^k and 7 x 2^k from 8 to N_g,
+    // multiples of 4 (a grid's M^2 points are a whole number of 16-point
+    // stages), ascending
     R.ngrid = 0;
     for (int m = 8; m <= ng; m *= 2)
-        for (int f : {2, 3, 5})
+        for (int f : {2, 3, 5, 7})
             if (f * m / 2 <= ng && R.ngrid < kMaxLevels) R.grid[R.ngrid++] = f * m / 2;
     std::sort(R.grid, R.grid + R.ngrid);
     return true;

@@ -18,7 +18,7 @@
 namespace bisp {
 
 constexpr int kMaxRings = 64;     // N_r for N_g <= 1024 is 52
-constexpr int kMaxLevels = 24;    // reduction grids: 2^k, 3 x 2^k and 5 x 2^k from 8 to N_g (21 at 1024)
+constexpr int kMaxLevels = 32;    // reduction grids: 2^k, 3, 5, 7 x 2^k from 8 to N_g (27 at 1024)
 constexpr int kTileRows = 8;      // rows (r1, r2) of a Step-II register tile
 constexpr int kTileCols = 8;      // consecutive r3 of a Step-II register tile
 
@@ -33,7 +33,7 @@ struct Rings {
     double kperp[kMaxRings] = {};      // mode-averaged |u|, grid units
     int64_t count[kMaxRings] = {};
     int maxc[kMaxRings] = {};          // largest |u_x| of a member (= largest |u_y|)
-    int ngrid = 0;                     // reduction grids, ascending: M = 2^k, 3 x 2^k, 5 x 2^k,
+    int ngrid = 0;                     // reduction grids, ascending: M = F x 2^k (F = 1, 3, 5, 7),
     int grid[kMaxLevels] = {};         // 8 <= M <= N_g
 };
 

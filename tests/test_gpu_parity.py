@@ -83,7 +83,7 @@ def test_forward_transform_planes(c64):
 
 def test_step1_dfields_on_every_grid(c64):
     """Stored D fields of sampled combinations of every reduction grid in use
-    (2^q, 3 x 2^q and 5 x 2^q sides) against the oracle's direct evaluation."""
+    (sides F x 2^q, F = 1, 3, 5, 7) against the oracle's direct evaluation."""
     tab = c64.plan.combo_table()
     rng = np.random.default_rng(3)
     seen = set()
@@ -101,8 +101,10 @@ def test_step1_dfields_on_every_grid(c64):
             want = O.dfield_at(c64.field64, c64.L, int(r), abs(int(n)), M)
             assert np.abs(got - want).max() < 2e-6 * max(np.abs(want).max(), 1e-30), key
     grids = {int(M) for M, _, _ in seen}
-    assert any(M % 3 == 0 for M in grids) and any(M % 5 == 0 for M in grids), grids
-    assert any(M % 3 and M % 5 for M in grids), grids
+    assert grids == {int(M) for M in np.unique(tab["grid"])}
+    for f in (3, 5, 7):
+        assert any(M % f == 0 for M in grids), (f, grids)
+    assert any(M & (M - 1) == 0 for M in grids), grids
 
 
 def test_combination_table_matches_oracle(c64):

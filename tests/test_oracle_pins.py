@@ -96,30 +96,31 @@ def test_dfield_on_reduced_grids():
     assert abs(red4 - full) > 1e-6 * abs(full)
 
 
-def test_dfield_on_a_5x2q_grid():
-    """The same on a grid of 5 x 2^q points (M = 20 at N_g = 32, which M does
-    not divide): D at x = (N_g/M) y against the term-by-term ring sum, and the
-    reduced triple sum of rings 3, 5, 6 (|u_x| <= 3, 5, 6: the bound is 14)
-    exact on M = 16 and 20, wrong on M = 12."""
+def test_dfield_on_5x2q_and_7x2q_grids():
+    """The same on grids of 5 x 2^q and 7 x 2^q points (M = 20 and 28 at
+    N_g = 32, which neither divides): D at x = (N_g/M) y against the
+    term-by-term ring sum, and the reduced triple sum of rings 3, 5, 6
+    (|u_x| <= 3, 5, 6: the bound is 14) exact on M = 16, 20 and 28, wrong on
+    M = 12."""
     ng, L = 32, 500.0
     d = synth.make_field(ng, L, 5)
     cube = np.fft.fftn(d) * (L ** 3 / ng ** 3)
     cube[0, 0, 0] = 0
     edges, kp, cnt = O.rings(ng)
-    M = 20
-    y = np.arange(M)
-    for r, n in [(3, 1), (5, -2)]:
-        got = O.dfield_at(d, L, r, n, M)
-        want = np.zeros((M, M), complex)
-        for i in range(-ng // 2, ng // 2):
-            for j in range(-ng // 2, ng // 2):
-                if not (edges[r] <= math.hypot(i, j) < edges[r + 1]):
-                    continue
-                want += cube[i % ng, j % ng, n % ng] * np.exp(-2j * np.pi * (i * y[:, None] + j * y[None, :]) / M)
-        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), (r, n)
+    for M in (20, 28):
+        y = np.arange(M)
+        for r, n in [(3, 1), (5, -2)]:
+            got = O.dfield_at(d, L, r, n, M)
+            want = np.zeros((M, M), complex)
+            for i in range(-ng // 2, ng // 2):
+                for j in range(-ng // 2, ng // 2):
+                    if not (edges[r] <= math.hypot(i, j) < edges[r + 1]):
+                        continue
+                    want += cube[i % ng, j % ng, n % ng] * np.exp(-2j * np.pi * (i * y[:, None] + j * y[None, :]) / M)
+            assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max(), (M, r, n)
     trip = [(3, 1), (5, 1), (6, -2)]
     full = np.sum(np.prod([O.dfield(d, L, r, n) for r, n in trip], axis=0))
-    for M in (16, 20):
+    for M in (16, 20, 28):
         red = np.sum(np.prod([O.dfield_at(d, L, r, n, M) for r, n in trip], axis=0)) * (ng / M) ** 2
         assert abs(red - full) <= 1e-12 * abs(full), M
     red12 = np.sum(np.prod([O.dfield_at(d, L, r, n, 12) for r, n in trip], axis=0)) * (ng / 12) ** 2
