@@ -438,7 +438,7 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
         int best = 0;
         float best_ms = 1e30f;
         for (int w : {2, 4, 8, 16, 32}) {
-            if (w > M || size_t(2) * w * (M + 1) * sizeof(C) > 227 * 1024) continue;
+            if (w > M || size_t(2) * w * fft_stride(M) * sizeof(C) > 227 * 1024) continue;
             if (launch(w) != cudaSuccess) return -1;
             cudaEventRecord(e0, s);
             for (int r = 0; r < 3; ++r) launch(w);

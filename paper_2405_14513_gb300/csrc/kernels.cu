@@ -75,6 +75,12 @@ struct DivIter {
     }
 };
 
+// Shared-memory position of element i of a transform row: a padding slot
+// after every 8 elements, so that the strided stores of the first radix-8
+// stages (elements 8 and 64 apart) fall in different banks.  A row takes
+// fft_stride(M) elements (kernels.cuh).
+__device__ __forceinline__ int spos(int i) { return i + (i >> 3); }
+
 // Stockham transform of nrows rows of length M = F x 2^q (F = 1, 3, 5 or 7)
 // held in shared memory (row stride P), X_k = sum_j x_j exp(-2 pi i jk / M):
 // one radix-F stage first when F > 1, then radix-8 stages and, for what is
@@ -95,16 +101,16 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
         const Rr h = Rr(0.86602540378443864676);   // sqrt(3)/2
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             const int row = t >> p, j = t & (third - 1);
-            const C v0 = a[row * P + j], v1 = a[row * P + j + third], v2 = a[row * P + j + 2 * third];
+            const C v0 = a[row * P + spos(j)], v1 = a[row * P + spos(j + third)], v2 = a[row * P + spos(j + 2 * third)];
             const Rr sx = v1.x + v2.x, sy = v1.y + v2.y, dx = v1.x - v2.x, dy = v1.y - v2.y;
             const Rr mx = v0.x - Rr(0.5) * sx, my = v0.y - Rr(0.5) * sy;
             C y0, y1, y2;
             y0.x = v0.x + sx; y0.y = v0.y + sy;
             y1.x = mx + h * dy; y1.y = my - h * dx;
             y2.x = mx - h * dy; y2.y = my + h * dx;
-            b[row * P + 3 * j] = y0;
-            b[row * P + 3 * j + 1] = y1;
-            b[row * P + 3 * j + 2] = y2;
+            b[row * P + spos(3 * j)] = y0;
+            b[row * P + spos(3 * j + 1)] = y1;
+            b[row * P + spos(3 * j + 2)] = y2;
         }
         __syncthreads();
         C *t2 = a;
@@ -124,8 +130,8 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
         for (int t = threadIdx.x; t < total; t += blockDim.x) {
             const int row = t >> p, j = t & (fifth - 1);
             const C *src = a + row * P;
-            const C v0 = src[j], v1 = src[j + fifth], v2 = src[j + 2 * fifth], v3 = src[j + 3 * fifth],
-                    v4 = src[j + 4 * fifth];
+            const C v0 = src[spos(j)], v1 = src[spos(j + fifth)], v2 = src[spos(j + 2 * fifth)], v3 = src[spos(j + 3 * fifth)],
+                    v4 = src[spos(j + 4 * fifth)];
             const C s1 = cadd(v1, v4), s2 = cadd(v2, v3), d1 = csub(v1, v4), d2 = csub(v2, v3);
             C a1, a2, b1, b2;
             a1.x = v0.x + c1 * s1.x + c2 * s2.x; a1.y = v0.y + c1 * s1.y + c2 * s2.y;
@@ -135,11 +141,11 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
             // -i b = (b.y, -b.x)
             C *dst = b + row * P;
             C y;
-            y.x = v0.x + s1.x + s2.x; y.y = v0.y + s1.y + s2.y; dst[5 * j] = y;
-            y.x = a1.x + b1.y; y.y = a1.y - b1.x; dst[5 * j + 1] = y;
-            y.x = a2.x + b2.y; y.y = a2.y - b2.x; dst[5 * j + 2] = y;
-            y.x = a2.x - b2.y; y.y = a2.y + b2.x; dst[5 * j + 3] = y;
-            y.x = a1.x - b1.y; y.y = a1.y + b1.x; dst[5 * j + 4] = y;
+            y.x = v0.x + s1.x + s2.x; y.y = v0.y + s1.y + s2.y; dst[spos(5 * j)] = y;
+            y.x = a1.x + b1.y; y.y = a1.y - b1.x; dst[spos(5 * j + 1)] = y;
+            y.x = a2.x + b2.y; y.y = a2.y - b2.x; dst[spos(5 * j + 2)] = y;
+            y.x = a2.x - b2.y; y.y = a2.y + b2.x; dst[spos(5 * j + 3)] = y;
+            y.x = a1.x - b1.y; y.y = a1.y + b1.x; dst[spos(5 * j + 4)] = y;
         }
         __syncthreads();
         C *t2 = a;
@@ -159,7 +165,7 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
             const C *src = a + row * P;
             C v[7];
 #pragma unroll
-            for (int k = 0; k < 7; ++k) v[k] = src[j + k * sev];
+            for (int k = 0; k < 7; ++k) v[k] = src[spos(j + k * sev)];
             const C s1 = cadd(v[1], v[6]), s2 = cadd(v[2], v[5]), s3 = cadd(v[3], v[4]);
             const C d1 = csub(v[1], v[6]), d2 = csub(v[2], v[5]), d3 = csub(v[3], v[4]);
             C am[3], bm[3];
@@ -171,12 +177,12 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
             bm[2].x = n3 * d1.x - n1 * d2.x + n2 * d3.x; bm[2].y = n3 * d1.y - n1 * d2.y + n2 * d3.y;
             C *dst = b + row * P;
             C y;
-            y.x = v[0].x + s1.x + s2.x + s3.x; y.y = v[0].y + s1.y + s2.y + s3.y; dst[7 * j] = y;
+            y.x = v[0].x + s1.x + s2.x + s3.x; y.y = v[0].y + s1.y + s2.y + s3.y; dst[spos(7 * j)] = y;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 // -i b = (b.y, -b.x)
-                y.x = am[m].x + bm[m].y; y.y = am[m].y - bm[m].x; dst[7 * j + m + 1] = y;
-                y.x = am[m].x - bm[m].y; y.y = am[m].y + bm[m].x; dst[7 * j + 6 - m] = y;
+                y.x = am[m].x + bm[m].y; y.y = am[m].y - bm[m].x; dst[spos(7 * j + m + 1)] = y;
+                y.x = am[m].x - bm[m].y; y.y = am[m].y + bm[m].x; dst[spos(7 * j + 6 - m)] = y;
             }
         }
         __syncthreads();
@@ -205,9 +211,9 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                 const int k = j - q * Ns;
                 const C *src = a + row * P;
                 C v[8];
-                v[0] = src[j];
+                v[0] = src[spos(j)];
 #pragma unroll
-                for (int r = 1; r < 8; ++r) v[r] = cmul(src[j + r * eighth], __ldg(&wt[(r * k) << sh]));
+                for (int r = 1; r < 8; ++r) v[r] = cmul(src[spos(j + r * eighth)], __ldg(&wt[(r * k) << sh]));
                 C e[4], o[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -232,10 +238,10 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                     C m1 = d02, m3 = d02;                 // d02 -/+ i d13
                     m1.x += d13.y; m1.y -= d13.x;
                     m3.x -= d13.y; m3.y += d13.x;
-                    dst[d0 + (0 + h) * Ns] = cadd(s02, s13);
-                    dst[d0 + (2 + h) * Ns] = m1;
-                    dst[d0 + (4 + h) * Ns] = csub(s02, s13);
-                    dst[d0 + (6 + h) * Ns] = m3;
+                    dst[spos(d0 + (0 + h) * Ns)] = cadd(s02, s13);
+                    dst[spos(d0 + (2 + h) * Ns)] = m1;
+                    dst[spos(d0 + (4 + h) * Ns)] = csub(s02, s13);
+                    dst[spos(d0 + (6 + h) * Ns)] = m3;
                 }
             }
             Ns *= 8;
@@ -252,21 +258,21 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                 const int q = divF(j >> s);
                 const int k = j - q * Ns;
                 const C *src = a + row * P;
-                const C v0 = src[j];
-                const C v1 = cmul(src[j + quarter], __ldg(&wt[k << sh]));
-                const C v2 = cmul(src[j + 2 * quarter], __ldg(&wt[(2 * k) << sh]));
-                const C v3 = cmul(src[j + 3 * quarter], __ldg(&wt[(3 * k) << sh]));
+                const C v0 = src[spos(j)];
+                const C v1 = cmul(src[spos(j + quarter)], __ldg(&wt[k << sh]));
+                const C v2 = cmul(src[spos(j + 2 * quarter)], __ldg(&wt[(2 * k) << sh]));
+                const C v3 = cmul(src[spos(j + 3 * quarter)], __ldg(&wt[(3 * k) << sh]));
                 const C s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
                 C *dst = b + row * P;
                 const int d0 = q * 4 * Ns + k;
-                dst[d0] = cadd(s02, s13);
-                dst[d0 + 2 * Ns] = csub(s02, s13);
+                dst[spos(d0)] = cadd(s02, s13);
+                dst[spos(d0 + 2 * Ns)] = csub(s02, s13);
                 // -i d13 = (d13.y, -d13.x)
                 C m1 = d02, m3 = d02;
                 m1.x += d13.y; m1.y -= d13.x;
                 m3.x -= d13.y; m3.y += d13.x;
-                dst[d0 + Ns] = m1;
-                dst[d0 + 3 * Ns] = m3;
+                dst[spos(d0 + Ns)] = m1;
+                dst[spos(d0 + 3 * Ns)] = m3;
             }
             Ns *= 4;
             s += 2;
@@ -279,11 +285,11 @@ __device__ C *fft_smem_f(C *a, C *b, int M, int P, int nrows, const Twiddles<C> 
                 const int j = t - row * half;
                 const int q = divF(j >> s);
                 const int k = j - q * Ns;
-                C v0 = a[row * P + j];
-                C v1 = cmul(a[row * P + j + half], __ldg(&wt[k << sh]));
+                C v0 = a[row * P + spos(j)];
+                C v1 = cmul(a[row * P + spos(j + half)], __ldg(&wt[k << sh]));
                 const int idx = q * 2 * Ns + k;
-                b[row * P + idx] = cadd(v0, v1);
-                b[row * P + idx + Ns] = csub(v0, v1);
+                b[row * P + spos(idx)] = cadd(v0, v1);
+                b[row * P + spos(idx + Ns)] = csub(v0, v1);
             }
             Ns *= 2;
             s += 1;
@@ -318,7 +324,7 @@ k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     in = field_ptr(in, fs_in);
     out = field_ptr(out, fs_out);
-    const int P = M + 1;
+    const int P = fft_stride(M);
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t row0 = int64_t(blockIdx.x) * rt;
@@ -326,14 +332,14 @@ k_fft_z_real(const R *__restrict__ in, typename Cx<R>::T *__restrict__ out, int 
     DivIter ld(threadIdx.x, blockDim.x, M);
     for (int t = threadIdx.x; t < nrow * M; t += blockDim.x, ld.next()) {
         const int r = ld.q, j = ld.r;
-        a[r * P + j] = cmk<C>(double(in[(row0 + r) * M + j]), 0.0);
+        a[r * P + spos(j)] = cmk<C>(double(in[(row0 + r) * M + j]), 0.0);
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nrow, tw);
     DivIter st(threadIdx.x, blockDim.x, nrow);
     for (int t = threadIdx.x; t < nkeep * nrow; t += blockDim.x, st.next()) {
         const int k = st.q, r = st.r;
-        out[int64_t(k) * rows + row0 + r] = res[r * P + k];
+        out[int64_t(k) * rows + row0 + r] = res[r * P + spos(k)];
     }
 }
 
@@ -347,7 +353,7 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
     extern __shared__ __align__(16) unsigned char smem_raw[];
     in = field_ptr(in, fs);
     out = field_ptr(out, fs);
-    const int P = M + 1;
+    const int P = fft_stride(M);
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t bt = blockIdx.x / ntile;
@@ -358,7 +364,7 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
     DivIter ld(threadIdx.x, blockDim.x, M);
     for (int t = threadIdx.x; t < nr * M; t += blockDim.x, ld.next()) {
         const int r = ld.q, j = ld.r;
-        a[r * P + j] = src[int64_t(row0 + r) * M + j];
+        a[r * P + spos(j)] = src[int64_t(row0 + r) * M + j];
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nr, tw);
@@ -366,7 +372,7 @@ k_fft_rows_T(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__rest
     DivIter st(threadIdx.x, blockDim.x, nr);
     for (int t = threadIdx.x; t < M * nr; t += blockDim.x, st.next()) {
         const int k = st.q, r = st.r;
-        C v = res[r * P + k];
+        C v = res[r * P + spos(k)];
         v.x *= scale;
         v.y *= scale;
         if (zero_dc && bt == 0 && row0 + r == 0 && k == 0) v = cmk<C>(0.0, 0.0);
@@ -384,7 +390,7 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     extern __shared__ __align__(16) unsigned char smem_raw[];
     planes = field_ptr(planes, fs);
     gt = field_ptr(gt, fs);
-    const int P = M + 1;
+    const int P = fft_stride(M);
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + rt * P;
     const int64_t jb = blockIdx.x / ntile;
@@ -425,7 +431,7 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
                 }
             }
         }
-        a[tr * P + j] = cmk<C>(double(vr), double(vi));
+        a[tr * P + spos(j)] = cmk<C>(double(vr), double(vi));
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nr, tw);
@@ -434,7 +440,7 @@ k_ring_gather(const typename Cx<R>::T *__restrict__ planes, int ng, RingArg ring
     DivIter st(threadIdx.x, blockDim.x, M);
     for (int t = threadIdx.x; t < M * nr; t += blockDim.x, st.next()) {
         const int r = st.q, k = st.r;
-        dst[t] = res[r * P + k];
+        dst[t] = res[r * P + spos(k)];
     }
 }
 
@@ -452,7 +458,7 @@ k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     in = field_ptr(in, fs);
     out = field_ptr(out, fs);
-    const int P = M + 1;
+    const int P = fft_stride(M);
     C *a = reinterpret_cast<C *>(smem_raw);
     C *b = a + w * P;
     const int64_t jb = blockIdx.x / ntile;
@@ -463,7 +469,7 @@ k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restri
     DivIter ld(threadIdx.x, blockDim.x, nc);
     for (int t = threadIdx.x; t < M * nc; t += blockDim.x, ld.next()) {
         const int i = ld.q, c = ld.r;
-        a[c * P + i] = (i <= mc || i >= M - mc) ? src[int64_t(i) * M + c] : cmk<C>(0.0, 0.0);
+        a[c * P + spos(i)] = (i <= mc || i >= M - mc) ? src[int64_t(i) * M + c] : cmk<C>(0.0, 0.0);
     }
     __syncthreads();
     const C *res = fft_smem(a, b, M, P, nc, tw);
@@ -471,7 +477,7 @@ k_fft_cols(const typename Cx<R>::T *__restrict__ in, typename Cx<R>::T *__restri
     DivIter st(threadIdx.x, blockDim.x, nc);
     for (int t = threadIdx.x; t < M * nc; t += blockDim.x, st.next()) {
         const int k = st.q, c = st.r;
-        dst[int64_t(k) * M + c] = res[c * P + k];
+        dst[int64_t(k) * M + c] = res[c * P + spos(k)];
     }
 }
 
@@ -815,7 +821,7 @@ cudaError_t launch_fft_z_real(const R *in, typename Cx<R>::T *out, int ng, int64
 {
     using C = typename Cx<R>::T;
     if (rt <= 0) rt = int(fft_rows_per_block(ng, sizeof(C)));
-    const size_t smem = size_t(2) * rt * (ng + 1) * sizeof(C);
+    const size_t smem = size_t(2) * rt * fft_stride(ng) * sizeof(C);
     const int64_t nblk = (rows + rt - 1) / rt;
     k_fft_z_real<R><<<dim3(unsigned(nblk), fb.nf), 256, smem, s>>>(in, out, ng, rows, nkeep, rt, tw, fb.fs_in,
                                                                    fb.fs_out);
@@ -830,7 +836,7 @@ cudaError_t launch_fft_rows_T(const typename Cx<R>::T *in, typename Cx<R>::T *ou
     using C = typename Cx<R>::T;
     if (rt <= 0) rt = int(fft_rows_per_block(M, sizeof(C)));
     rt = std::min(rt, nrow);
-    const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
+    const size_t smem = size_t(2) * rt * fft_stride(M) * sizeof(C);
     const int ntile = (nrow + rt - 1) / rt;
     const int64_t nblk = nb * ntile;
     if (nblk == 0) return cudaSuccess;
@@ -847,7 +853,7 @@ cudaError_t launch_ring_gather(const typename Cx<R>::T *planes, int ng, const Ri
     using C = typename Cx<R>::T;
     if (rt <= 0) rt = int(fft_rows_per_block(M, sizeof(C)));
     rt = std::min(rt, M);
-    const size_t smem = size_t(2) * rt * (M + 1) * sizeof(C);
+    const size_t smem = size_t(2) * rt * fft_stride(M) * sizeof(C);
     const int ntile = (M + rt - 1) / rt;
     const int64_t nblk = njobs * ntile;
     if (nblk == 0) return cudaSuccess;
@@ -867,7 +873,7 @@ cudaError_t launch_fft_cols(const typename Cx<R>::T *in, typename Cx<R>::T *out,
     using C = typename Cx<R>::T;
     if (w <= 0) w = 8;
     w = std::min(w, M);
-    const size_t smem = size_t(2) * w * (M + 1) * sizeof(C);
+    const size_t smem = size_t(2) * w * fft_stride(M) * sizeof(C);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     const int ntile = (M + w - 1) / w;
     const int64_t nblk = njobs * ntile;

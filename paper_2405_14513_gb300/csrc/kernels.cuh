@@ -189,5 +189,9 @@ cudaError_t launch_ntri(const double2 *ifields, const int64_t *ioff, const int32
 // launchers above selects this with the default 16 KB; the plan's autotuner
 // passes its own choice.
 size_t fft_rows_per_block(int M, size_t elem, size_t bytes = 16384);
+// Elements of one row of a transform's shared-memory buffers: M values with
+// a padding slot after every 8, and one more so that consecutive rows start
+// in different banks.
+inline __host__ __device__ constexpr int fft_stride(int M) { return M + (M >> 3) + 1; }
 
 }  // namespace bisp
