@@ -359,10 +359,13 @@ int init_attributes()
 // leave one block per SM).  For the forward z pass, the forward row passes
 // and each reduction grid's gather, candidate tiles of 4-64 KB per buffer,
 // and for each grid's second pass strips of 2-32 columns, are timed on
-// scratch buffers holding a sample of the plan's rows (at most 64 fields of
-// a grid, 16 planes, 64K z rows), and the fastest is kept.  Rows and
-// columns are transformed independently, so the choice changes the speed,
-// not the results.
+// scratch buffers holding a sample of the plan's rows (16 planes, 64K z
+// rows, and at most kTuneJobs fields of a grid, evenly spaced over its
+// fields so that their rings, and the launch's size, are those of the
+// estimate), and the fastest is kept.  Rows and columns are transformed
+// independently, so the choice changes the speed, not the results.
+constexpr int64_t kTuneJobs = 512;
+
 template <typename R>
 int autotune_transforms(bisp_plan *p, cudaStream_t s)
 {
@@ -375,8 +378,21 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     if constexpr (sizeof(R) == 8) tw = p->tw_d; else tw = p->tw_f;
     const int64_t zrows = std::min<int64_t>(ng2, 65536);
     const int64_t npl = std::min<int64_t>(nz1, 16);
-    int64_t jmax = 0;
-    for (const Level &L : P.levels) jmax = std::max(jmax, std::min<int64_t>(L.njobs, 64) * L.M * L.M);
+    // the sampled fields of every grid: every stride-th of its (plane, ring)
+    // fields, in the estimate's order, at most kTuneJobs
+    std::vector<std::vector<Job>> sample(P.levels.size());
+    int64_t jmax = 0, nsamp = 0;
+    for (size_t l = 0; l < P.levels.size(); ++l) {
+        const Level &L = P.levels[l];
+        const int64_t stride = (L.njobs + kTuneJobs - 1) / kTuneJobs;
+        int64_t k = 0;
+        for (int n = 0; n <= Rg.nz; ++n)
+            for (int r = 0; r < Rg.nr; ++r)
+                if (P.doff[(size_t(L.lev) * (Rg.nz + 1) + n) * kMaxRings + r] >= 0 && k++ % stride == 0)
+                    sample[l].push_back(Job{n, r, 0});
+        jmax = std::max(jmax, int64_t(sample[l].size()) * L.M * L.M);
+        nsamp += int64_t(sample[l].size());
+    }
     // scratch: z-pass input and output, the transformed planes (input of the
     // gathers), and two buffers for the row passes
     const size_t bz = size_t(zrows) * ng * sizeof(R);
@@ -395,13 +411,21 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     C *planes = static_cast<C *>(talloc(bplanes));
     C *b0 = static_cast<C *>(talloc(bout));
     C *b1 = static_cast<C *>(talloc(brows));
-    // output offsets of the sample jobs of every grid (job j at j M^2)
-    int64_t *d_offs = static_cast<int64_t *>(talloc(sizeof(int64_t) * 64 * P.levels.size()));
-    std::vector<int64_t> h_offs(64 * P.levels.size());
-    for (size_t l = 0; l < P.levels.size(); ++l)
-        for (int j = 0; j < 64; ++j) h_offs[64 * l + j] = int64_t(j) * P.levels[l].M * P.levels[l].M;
+    // the sampled jobs and their output offsets (job j of a grid at j M^2)
+    int64_t *d_offs = static_cast<int64_t *>(talloc(sizeof(int64_t) * size_t(nsamp)));
+    Job *d_samp = static_cast<Job *>(talloc(sizeof(Job) * size_t(nsamp)));
+    std::vector<int64_t> h_offs;
+    std::vector<Job> h_samp;
+    std::vector<int64_t> samp0;
+    for (size_t l = 0; l < P.levels.size(); ++l) {
+        samp0.push_back(int64_t(h_samp.size()));
+        for (size_t j = 0; j < sample[l].size(); ++j) {
+            h_offs.push_back(int64_t(j) * P.levels[l].M * P.levels[l].M);
+            h_samp.push_back(sample[l][j]);
+        }
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (!zin || !planes || !b0 || !b1 || !d_offs || cudaEventCreate(&e0) != cudaSuccess ||
+    if (!zin || !planes || !b0 || !b1 || !d_offs || !d_samp || cudaEventCreate(&e0) != cudaSuccess ||
         cudaEventCreate(&e1) != cudaSuccess) {
         cudaGetLastError();
         cleanup();
@@ -413,6 +437,7 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     cudaMemsetAsync(b0, 0, bout, s);
     cudaMemsetAsync(b1, 0, brows, s);
     cudaMemcpyAsync(d_offs, h_offs.data(), h_offs.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(d_samp, h_samp.data(), h_samp.size() * sizeof(Job), cudaMemcpyHostToDevice, s);
     const size_t cand[] = {4096, 8192, 16384, 32768, 65536};
     // the fastest of the candidate rows per block for one launch
     auto pick = [&](int M, int cap, auto &&launch) -> int {
@@ -461,13 +486,14 @@ int autotune_transforms(bisp_plan *p, cudaStream_t s)
     if (p->rt_z < 0 || p->rt_xy < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
     for (size_t l = 0; l < P.levels.size() && !st; ++l) {
         const Level &L = P.levels[l];
-        const int64_t nj = std::min<int64_t>(L.njobs, 64);
-        const int64_t *d_off = d_offs + 64 * l;
+        const int64_t nj = int64_t(sample[l].size());
+        const int64_t *d_off = d_offs + samp0[l];
+        const Job *d_j = d_samp + samp0[l];
         const int g = pick(L.M, L.M, [&](int rt) {
-            return launch_ring_gather<R>(planes, ng, p->ring_arg, p->d_jobs[l], nj, L.M, false, b0, tw, one, s, rt);
+            return launch_ring_gather<R>(planes, ng, p->ring_arg, d_j, nj, L.M, false, b0, tw, one, s, rt);
         });
         const int r = pick_w(L.M, [&](int w) {
-            return launch_fft_cols<R>(b0, b1, L.M, nj, d_off, p->d_jobs[l], p->ring_arg, tw, one, s, w);
+            return launch_fft_cols<R>(b0, b1, L.M, nj, d_off, d_j, p->ring_arg, tw, one, s, w);
         });
         if (g < 0 || r < 0) st = fail(BISP_CUDA_ERROR, "transform autotuner");
         p->rt_gather[L.lev] = std::max(g, 0);
