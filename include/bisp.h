@@ -100,9 +100,11 @@ typedef struct {
     size_t resident_bytes;           /* device memory owned by the plan               */
     int n_views;                     /* binnings (bisp_view_info), >= 1                */
     int64_t out_doubles;             /* doubles of B per field (all views)            */
-    /* Step-II work on the tensor cores (MIXED_TC; 0 otherwise), in grid points: */
     double pair_products;            /* distinct pair products D1 D2 on those grids   */
-    double tc_row_points;            /* pair products the tiles form (rows x points)   */
+    /* Step-II work on the tensor cores (MIXED_TC; 0 otherwise), in grid points: */
+    double tc_row_points;            /* pair products the tiles form (rows x points;   */
+                                     /* each (pair, r1, r2) once, on the largest grid  */
+                                     /* its r3 need)                                    */
     double tc_lane_points;           /* tensor-memory lanes x points of all tiles      */
     double tc_mma_products;          /* lanes x window columns x points (MMA work)     */
     double tc_staged_bytes;          /* bytes the tiles copy from L2 into shared memory */

@@ -175,6 +175,47 @@ def test_multipoles_match_oracle(which, c64, c64_fp64):
     assert err.max() < TOL[which], err
 
 
+def _ring_maxc(ng):
+    """Largest |u_x| of the lattice members of each ring (edges from the oracle)."""
+    edges, _, _ = O.rings(ng)
+    i = np.arange(-(ng // 2), ng // 2)
+    ux, uy = np.meshgrid(i, i, indexing="ij")
+    rad = np.hypot(ux, uy)
+    return np.array([np.abs(ux[(rad >= edges[r]) & (rad < edges[r + 1])]).max() for r in range(len(edges) - 1)])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "mixed_tc"])
+def test_reduction_grids_are_exact_and_rows_share_one(prec):
+    """Every combination is summed on a grid of F x 2^q points (F = 1, 3, 5,
+    7; a multiple of 4) above its aliasing bound maxc1 + maxc2 + maxc3.  The
+    CUDA-core path takes the smallest such grid; the tensor-core path sums
+    every r3 of one (n1, n2, r1, r2) row on one grid, the smallest above the
+    largest bound among them."""
+    ng, L = 64, 1000.0
+    plan = api.Plan(ng, L, synth.default_k1_edges(ng, L, 6), 5, 5, 6, precision=prec)
+    tab = plan.combo_table()
+    plan.close()
+    grids = np.array(sorted({f * 2 ** q for f in (1, 3, 5, 7) for q in range(2, 10)
+                             if 8 <= f * 2 ** q <= ng}))
+    maxc = _ring_maxc(ng)
+    ints, M = tab["ints"], tab["grid"].astype(np.int64)
+    bound = maxc[ints[:, 3]] + maxc[ints[:, 4]] + maxc[ints[:, 5]]
+    assert np.all(np.isin(M, grids)) and np.all(M > bound)
+    smallest = grids[np.searchsorted(grids, bound + 1)]
+    if prec == "mixed":
+        assert np.array_equal(M, smallest)
+        return
+    rows = {}
+    for k, key in enumerate(map(tuple, ints[:, [0, 1, 3, 4]])):
+        rows.setdefault(key, []).append(k)
+    merged = 0
+    for idx in rows.values():
+        assert len(set(M[idx])) == 1
+        assert M[idx[0]] == smallest[idx].max()
+        merged += int(np.any(M[idx] > smallest[idx]))
+    assert merged > 0
+
+
 @pytest.mark.parametrize("prec", ["fp32", "mixed_tc"])
 def test_fp32_plain_and_tensor_core_paths(prec):
     c = Case(64, 1000.0, 6, 5, 5, 6, precision=prec, seed=2)
