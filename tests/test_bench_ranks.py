@@ -73,3 +73,23 @@ def test_launch_decision_spawns_or_refuses():
     r = subprocess.run([sys.executable, bench.__file__, "--gpus", "2"], env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode == 2 and "WORLD_SIZE=1" in r.stdout
+
+
+def test_step2_traffic_digest_covers_the_kernel_and_its_tiling():
+    """The DRAM figure of the bench line is reported only while the Step-II
+    source it was captured on is unchanged: every region of that source (the
+    kernel, the tile limits, the grid set and the tiling) must be found, and
+    a capture whose digest differs is refused."""
+    import json
+    import bench
+    for prec in bench.STEP2_SOURCE:
+        d = bench._kernel_digest(prec)
+        assert len(d) == 16 and int(d, 16) >= 0
+    with open(os.path.join(bench.ROOT, "profiles", "step2_dram_mixed_tc.json")) as fh:
+        rec = json.load(fh)
+    assert {int(c["n_g"]) for c in rec["captures"]} >= {512}
+    if rec["kernel_digest"] == bench._kernel_digest("mixed_tc"):
+        assert bench._traffic(512, "mixed_tc")[0] == float(rec["captures"][0]["bytes_per_estimate"])
+    else:
+        assert bench._traffic(512, "mixed_tc")[0] is None
+    assert bench._traffic(100, "mixed_tc")[0] is None
