@@ -25,11 +25,12 @@ from oracle import oracle as O
 from paper_2405_14513_gb300 import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-NG, L, NK1, NMU = 64, 1000.0, 6, 5
+# (N_g, L, k1 bins, (mu, t) bins): a 2^k and a 3 x 2^k grid
+CASES = {64: (64, 1000.0, 6, 5), 48: (48, 800.0, 6, 5)}
 
 
 @pytest.fixture(scope="module")
-def plans(tmp_path_factory):
+def driver(tmp_path_factory):
     if shutil.which("g++") is None:
         pytest.skip("no g++")
     d = tmp_path_factory.mktemp("plan_host")
@@ -38,6 +39,15 @@ def plans(tmp_path_factory):
     subprocess.run(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-I", os.path.join(ROOT, "include"), "-I", src,
                     os.path.join(ROOT, "tests", "plan_host_check.cpp"), os.path.join(src, "plan.cpp"), "-o", exe,
                     "-lpthread"], check=True)
+    return d, exe
+
+
+@pytest.fixture(scope="module", params=sorted(CASES))
+def plans(request, driver):
+    d, exe = driver
+    NG, L, NK1, NMU = CASES[request.param]
+    d = d / f"ng{NG}"
+    d.mkdir()
     ntri, _ = O.ntri(NG)
     ntri.astype(np.int64).tofile(str(d / "ntri.bin"))
     edges = synth.default_k1_edges(NG, L, NK1)
@@ -54,7 +64,7 @@ def plans(tmp_path_factory):
             "tcrows": np.fromfile(pre + ".tcrows", dtype=np.int64).reshape(nt, 7),
             "missing": missing,
         }
-    out["edges"] = edges
+    out.update(edges=edges, ng=NG, L=L, nmu=NMU)
     return out
 
 
@@ -67,7 +77,7 @@ def _ring_maxc(ng):
 
 
 def test_combinations_match_the_oracle(plans):
-    ref = O.combos(NG, L, plans["edges"], NMU, NMU, half_space=True)
+    ref = O.combos(plans["ng"], plans["L"], plans["edges"], plans["nmu"], plans["nmu"], half_space=True)
     want = {tuple(map(int, r)) for r in ref["ints"]}
     for tensor in (0, 1):
         got = [tuple(map(int, r)) for r in plans[tensor]["combos"][:, :6]]
@@ -76,6 +86,7 @@ def test_combinations_match_the_oracle(plans):
 
 
 def test_grids_are_exact_and_chosen_by_the_rules(plans):
+    NG = plans["ng"]
     grids = np.array(sorted({f * 2 ** q for f in (1, 3, 5, 7) for q in range(2, 10) if 8 <= f * 2 ** q <= NG}))
     maxc = _ring_maxc(NG)
     for tensor in (0, 1):
